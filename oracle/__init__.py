@@ -1,0 +1,201 @@
+"""FP64 CPU oracle for the free-space spectral Poisson solver (arXiv 2405.02603).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the product.  It is independent of the
+CUDA path: no shared code, kernels, headers, tables or constant generators.
+
+The arithmetic lives in ``fsp_oracle.c`` (plain C, double precision); this
+module marshals numpy arrays to it and adds the analytic potentials and the
+error metrics.  Every function names the passage of the paper it follows:
+
+- ``fft1d``/``fft3d``: textbook recursive mixed-radix FFT (the FFT of Sec. 1,
+  convolution theorem); ``dft1d``: the DFT by definition.
+- ``dct1``/``dct1_3d``: type-I DCT by definition (Sec. 2.4).
+- ``kernel_T``: real-space kernel of Hockney-Eastwood (Sec. 2.2, step 3),
+  Vico-Greengard on (4N)^3 (Sec. 2.3, Eq. green_vico) or its DCT-I variant on
+  (2N+1)^3 (Sec. 2.4).
+- ``solve_fft``: Sec. 2.2 steps 1-5 on the full doubled grid.
+- ``solve_direct``: the O(N_g^2) discrete convolution sum (Sec. 1).
+- ``spectrum``: the multiplier h^3 DFT{G_2}/(2N)^3 on the non-redundant octant.
+- ``analytic``: the Gaussian (Sec. 3.1, Eq. gaussian) and uniform-sphere
+  (Sec. 3.1, Eq. sphere) potentials, in this project's sign convention.
+"""
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+HE, VG, VG_DCT = 0, 1, 2
+ALGOS = {"he": HE, "vg": VG, "vg_dct": VG_DCT}
+ALPHA = 1.1  # Vico-Greengard window factor, Sec. 2.3
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lp = ctypes.POINTER(ctypes.c_longlong)
+        i, d = ctypes.c_int, ctypes.c_double
+        lib.orc_num_threads.restype = i
+        lib.orc_set_num_threads.argtypes = [i]
+        lib.orc_dft1d.argtypes = [i, dp, dp, i]
+        lib.orc_fft1d.argtypes = [i, dp, dp, i]
+        lib.orc_fft3d.argtypes = [i, i, i, dp, i]
+        lib.orc_dct1_1d.argtypes = [i, dp, dp]
+        lib.orc_dct1_3d.argtypes = [i, i, dp, dp]
+        lib.orc_green_vico_hat.argtypes = [d, d]
+        lib.orc_green_vico_hat.restype = d
+        lib.orc_vg_full.argtypes = [i, d, d, dp, dp]
+        lib.orc_kernel_T.argtypes = [i, i, d, d, dp]
+        lib.orc_solve_fft.argtypes = [i, d, dp, dp, dp]
+        lib.orc_spectrum.argtypes = [i, d, dp, dp]
+        lib.orc_solve_direct.argtypes = [i, d, dp, dp, lp, ctypes.c_longlong, dp]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def num_threads():
+    return _load().orc_num_threads()
+
+
+def set_num_threads(n):
+    _load().orc_set_num_threads(int(n))
+
+
+def _c128(x):
+    return np.ascontiguousarray(x, dtype=np.complex128)
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def dft1d(x, sign=-1):
+    """X[k] = sum_j x[j] exp(sign 2 pi i jk/n), by definition (O(n^2))."""
+    x = _c128(x)
+    out = np.empty_like(x)
+    _load().orc_dft1d(x.size, _p(x), _p(out), int(sign))
+    return out
+
+
+def fft1d(x, sign=-1):
+    """Unnormalised textbook mixed-radix FFT of a 1D array."""
+    x = _c128(x)
+    out = np.empty_like(x)
+    _load().orc_fft1d(x.size, _p(x), _p(out), int(sign))
+    return out
+
+
+def fft3d(a, sign=-1):
+    """Unnormalised 3D FFT of a (nz, ny, nx) array (returns a new array)."""
+    a = _c128(a).copy()
+    nz, ny, nx = a.shape
+    _load().orc_fft3d(nx, ny, nz, _p(a), int(sign))
+    return a
+
+
+def dct1(x):
+    """Unnormalised DCT-I of M+1 samples (REDFT00 convention), by definition."""
+    x = _f64(x)
+    out = np.empty_like(x)
+    _load().orc_dct1_1d(x.size - 1, _p(x), _p(out))
+    return out
+
+
+def dct1_3d(x, K=None):
+    """3D DCT-I of a (M+1)^3 array, evaluated at outputs [0,K]^3."""
+    x = _f64(x)
+    M = x.shape[0] - 1
+    assert x.shape == (M + 1,) * 3
+    K = M if K is None else int(K)
+    out = np.empty((K + 1,) * 3, dtype=np.float64)
+    _load().orc_dct1_3d(M, K, _p(x), _p(out))
+    return out
+
+
+def green_vico_hat(kabs, Lt):
+    """Eq. green_vico, G_L(k) = 2 (sin(L_t |k|/2)/|k|)^2 (scalar)."""
+    return _load().orc_green_vico_hat(float(kabs), float(Lt))
+
+
+def window(L, alpha=ALPHA):
+    """Truncation window L_t = alpha sqrt(3) L for the cube of side L (Sec. 2.3)."""
+    return alpha * np.sqrt(3.0) * L
+
+
+def kernel_T(algo, N, L=1.0, alpha=ALPHA):
+    """Real-space kernel T[m], m in [0,N]^3, shape (N+1,)*3 indexed [z,y,x]."""
+    algo = ALGOS.get(algo, algo)
+    T = np.empty((N + 1,) * 3, dtype=np.float64)
+    _load().orc_kernel_T(int(algo), int(N), float(L), float(alpha), _p(T))
+    return T
+
+
+def vg_full(N, L=1.0, alpha=ALPHA):
+    """Vico-Greengard (4N)^3 inverse transform (complex) and its restriction T."""
+    h = L / N
+    full = np.empty((4 * N,) * 3, dtype=np.complex128)
+    T = np.empty((N + 1,) * 3, dtype=np.float64)
+    _load().orc_vg_full(int(N), float(h), float(window(L, alpha)), _p(full), _p(T))
+    return full, T
+
+
+def spectrum(T, h):
+    """S[q] = h^3 DFT_{2N}{G_2}[q] / (2N)^3 for q in [0,N]^3 (real part)."""
+    T = _f64(T)
+    N = T.shape[0] - 1
+    S = np.empty_like(T)
+    _load().orc_spectrum(N, float(h), _p(T), _p(S))
+    return S
+
+
+def solve_fft(T, rho, h):
+    """Hockney-Eastwood steps 1-5 on the full doubled grid with kernel T."""
+    T, rho = _f64(T), _f64(rho)
+    N = rho.shape[0]
+    assert rho.shape == (N, N, N) and T.shape == (N + 1,) * 3
+    phi = np.empty_like(rho)
+    _load().orc_solve_fft(N, float(h), _p(T), _p(rho), _p(phi))
+    return phi
+
+
+def solve_direct(T, rho, h, points=None):
+    """phi_i = h^3 sum_j T[|i-j|] rho_j, at flat indices `points` (or all)."""
+    T, rho = _f64(T), _f64(rho)
+    N = rho.shape[0]
+    assert rho.shape == (N, N, N) and T.shape == (N + 1,) * 3
+    lib = _load()
+    if points is None:
+        out = np.empty_like(rho)
+        lib.orc_solve_direct(N, float(h), _p(T), _p(rho), None, 0, _p(out))
+        return out
+    pts = np.ascontiguousarray(points, dtype=np.int64).ravel()
+    assert pts.size == 0 or (pts.min() >= 0 and pts.max() < N ** 3)
+    out = np.empty(pts.size, dtype=np.float64)
+    lib.orc_solve_direct(N, float(h), _p(T), _p(rho),
+                         pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), pts.size, _p(out))
+    return out
+
+
+def solve(algo, rho, L=1.0, alpha=ALPHA):
+    """Kernel construction plus FFT solve for one source (convenience)."""
+    N = rho.shape[0]
+    T = kernel_T(algo, N, L, alpha)
+    return solve_fft(T, rho, L / N)
+
+
+from . import analytic  # noqa: E402  (pure-numpy helpers, no C)
+
+__all__ = ["HE", "VG", "VG_DCT", "ALPHA", "dft1d", "fft1d", "fft3d", "dct1", "dct1_3d",
+           "green_vico_hat", "window", "kernel_T", "vg_full", "spectrum", "solve_fft",
+           "solve_direct", "solve", "analytic", "num_threads", "set_num_threads"]
+

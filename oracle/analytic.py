@@ -1,0 +1,66 @@
+"""Closed-form potentials and error metrics used to pin the oracle.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Sign convention of this
+project: phi = G * rho with G = +1/(4 pi |x|), i.e. Lap(phi) = -rho (Sec. 1,
+Eq. poisson_eq with eps0 = 1).  The paper's Gaussian test (Sec. 3.1, Eq.
+gaussian) prints a negative source with a positive potential; here the source
+is the positive unit-charge Gaussian and the potential is the same positive
+erf(r / (sqrt(2) sigma)) / (4 pi r).
+"""
+import numpy as np
+from scipy.special import erf
+
+
+def cell_centres(N, L):
+    """Cell-centred coordinates x_i = -L/2 + (i + 1/2) h, h = L/N."""
+    h = L / N
+    return -0.5 * L + (np.arange(N) + 0.5) * h
+
+
+def _radius(N, L, centre):
+    c = cell_centres(N, L)
+    z = c[:, None, None] - centre[2]
+    y = c[None, :, None] - centre[1]
+    x = c[None, None, :] - centre[0]
+    return np.sqrt(x * x + y * y + z * z)
+
+
+def gaussian_potential(N, L=1.0, sigma=0.05, centre=(0.0, 0.0, 0.0), weight=1.0):
+    """Potential of weight * (unit-charge Gaussian of width sigma) (Sec. 3.1).
+
+    phi(r) = weight * erf(r / (sqrt(2) sigma)) / (4 pi r), with the r -> 0 limit
+    weight * sqrt(2/pi) / (4 pi sigma).  Shape (N, N, N), index [z, y, x].
+    """
+    r = _radius(N, L, centre)
+    out = np.empty_like(r)
+    small = r < 1e-12
+    rr = r[~small]
+    out[~small] = erf(rr / (np.sqrt(2.0) * sigma)) / (4.0 * np.pi * rr)
+    out[small] = np.sqrt(2.0 / np.pi) / (4.0 * np.pi * sigma)
+    return weight * out
+
+
+def sphere_potential(N, L=2.4, radius=1.0, density=1.0, centre=(0.0, 0.0, 0.0)):
+    """Potential of a uniform ball (Sec. 3.1, Eq. sphere), this sign convention.
+
+    Inside: density (3 R^2 - r^2) / 6; outside: density R^3 / (3 r).
+    """
+    r = _radius(N, L, centre)
+    R = radius
+    inside = density * (3.0 * R * R - r * r) / 6.0
+    outside = density * R ** 3 / (3.0 * np.maximum(r, 1e-300))
+    return np.where(r <= R, inside, outside)
+
+
+def e_max(phi, ref):
+    """max_i |phi_i - ref_i| / max_i |ref_i| (the tolerance metric)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(phi - ref)) / np.max(np.abs(ref)))
+
+
+def rel_l2(phi, ref):
+    """||phi - ref||_2 / ||ref||_2 over the mesh points (Sec. 3.1)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm((phi - ref).ravel()) / np.linalg.norm(ref.ravel()))

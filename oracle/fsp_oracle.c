@@ -413,6 +413,9 @@ void orc_spectrum(int N, double h, const double *T, double *S) {
  * The discrete convolution by its definition (Sec. 1, the O(N_g^2) sum):
  *   phi_i = h^3 sum_{j in [0,N)^3} T[|i_x-j_x|, |i_y-j_y|, |i_z-j_z|] rho_j
  * evaluated at the `npts` flat output indices `pts` (all N^3 if pts == NULL).
+ * The N^3 products are accumulated with Neumaier's compensated summation, so
+ * the sum is exact to a few roundings whatever N (plain accumulation of N^3
+ * terms drifts by about N^3 eps).
  */
 void orc_solve_direct(int N, double h, const double *T, const double *rho, const long long *pts, long long npts,
                       double *out) {
@@ -422,13 +425,21 @@ void orc_solve_direct(int N, double h, const double *T, const double *rho, const
     for (long long p = 0; p < total; ++p) {
         long long i = pts ? pts[p] : p;
         int ix = (int)(i % N), iy = (int)((i / N) % N), iz = (int)(i / ((long long)N * N));
-        double acc = 0.0;
+        double sum = 0.0, comp = 0.0;
         for (int jz = 0; jz < N; ++jz)
             for (int jy = 0; jy < N; ++jy) {
                 const double *Trow = T + ((size_t)abs(iz - jz) * k1 + abs(iy - jy)) * k1;
                 const double *rrow = rho + ((size_t)jz * N + jy) * N;
-                for (int jx = 0; jx < N; ++jx) acc += Trow[abs(ix - jx)] * rrow[jx];
+                for (int jx = 0; jx < N; ++jx) {
+                    double t = Trow[abs(ix - jx)] * rrow[jx];
+                    double s = sum + t;
+                    if (fabs(sum) >= fabs(t))
+                        comp += (sum - s) + t;
+                    else
+                        comp += (t - s) + sum;
+                    sum = s;
+                }
             }
-        out[p] = h * h * h * acc;
+        out[p] = h * h * h * (sum + comp);
     }
 }

@@ -36,6 +36,19 @@ def test_fft_solve_equals_direct_sum(orc, algo, N):
     assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("algo", ["he", "vg_dct"])
+def test_direct_sum_accuracy_does_not_grow_with_n(orc, algo):
+    """The compensated direct sum and the FFT solve agree to a few ulps at
+    N = 64 and 96 (a plain running sum would drift by about N^3 eps)."""
+    for N in (64, 96):
+        rho = I.gaussian_mixture(N)
+        T = orc.kernel_T(algo, N)
+        fft = orc.solve_fft(T, rho, 1.0 / N).ravel()
+        pts = np.array([0, N ** 3 - 1, (N // 2) * (N * N + N + 1), 12345, 99999])
+        d = orc.solve_direct(T, rho, 1.0 / N, pts)
+        assert np.max(np.abs(fft[pts] - d)) <= 5e-15 * np.max(np.abs(d))
+
+
 def test_direct_sum_at_points_matches_full(orc):
     N = 7
     T = orc.kernel_T("he", N)

@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark: Vico-Greengard free-space solves/s at N=256 on one GB300.
+
+A step is one free-space solve (Sec. 2.2 steps 1-5 with the Vico-Greengard
+spectrum of Sec. 2.3): the five kernels pad+x-R2C, y-FFT, z-FFT*S*z-IFFT,
+y-IFFT, x-C2R, on an N^3 = 256^3 cell-centred grid of the unit cube, source
+a seeded 8-Gaussian mixture.  The headline `value` is the FP32-mixed form
+(single-precision transforms, FP64-precomputed spectrum); the FP64 form is
+reported beside it in `fp64`.  Each form states its max relative error against
+the FP64 CPU oracle (computed on the same source, when the CPU leg runs).
+
+Timing: W untimed warm-up solves, then exactly K solves between two CUDA
+events on the launching stream, with a device synchronise (and a barrier
+across ranks) on both sides.  Inputs rotate over 4 source/output buffer pairs
+and every solve streams about 1.8 GB (FP32) through HBM, far beyond the
+129 MB L2, so no step finds its input in L2.  Per-pass events recorded by the
+library's timing hook give each kernel's duration for the roofline object.
+
+--impl reference runs the FP64 CPU oracle (oracle/) on the same workload: a
+bounded number of full solves on the host cores.
+
+Multi-GPU: replicas only (independent solves per GPU, no collective in the
+data path); value = solves of all ranks / max time over ranks.
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import fsp_inputs as I  # noqa: E402
+
+METRIC = "VG free-space solves/s at N=256 (FP32-mix vs FP64, stated err); HBM GB/s; p99 ms"
+FALLBACK_HBM_GBS = 6800.0
+PASS_NAMES = ["k_r2c_rows (P1 pad+x-R2C)", "k_lines<fwd> (P2 y-FFT)", "k_lines<fwd*S*inv> (P3 z)",
+              "k_lines<inv> (P4 y-IFFT)", "k_c2r_rows (P5 x-C2R)"]
+NSRC = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="fsp", choices=["fsp", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--algo", default="vg", choices=["he", "vg", "vg_dct"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget-s", type=float, default=90.0)
+    return ap.parse_args()
+
+
+def pass_bytes(N, c, r):
+    """Algorithmic HBM bytes of each pass (read + write, nothing re-read)."""
+    a = N * N * (N + 1) * c  # one N x N x (N+1) complex volume
+    return [N ** 3 * r + a, a + 2 * a, 2 * a + 2 * a + (N + 1) ** 3 * r, 2 * a + a, a + N ** 3 * r]
+
+
+def solve_flops(N):
+    """Nominal flops per solve: 5 n log2 n per complex FFT of length n (the
+    length-N packed FFTs of the real rows included, pre/post ignored)."""
+    lg = np.log2
+    x = 2 * N * N * 5 * N * lg(N)                      # P1 + P5: N^2 rows, length-N complex FFT each
+    y = 2 * (N + 1) * N * 5 * (2 * N) * lg(2 * N)       # P2 + P4
+    z = 2 * (N + 1) * 2 * N * 5 * (2 * N) * lg(2 * N)   # P3: forward and inverse per line
+    return float(x + y + z)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_src_sha():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2405_02603_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(dtype, N, kernel_idx):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "solve_n%d_dram_traffic.json" % N)
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_src_sha") != kernel_src_sha():
+            return None
+        return d[dtype]["per_launch_bytes"][kernel_idx] * d[dtype].get("scale_to_full", 1.0)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            rows = [[x.strip() for x in ln.split(",")] for ln in f if ln.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_sources(N, dtype):
+    import torch
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    srcs, host = [], []
+    for i in range(NSRC):
+        rho = I.gaussian_mixture(N, seed=2405 + i).astype(np.float32)  # exact in both precisions
+        host.append(rho.astype(np.float64))
+        srcs.append(torch.from_numpy(rho).to(dtype=tdt).cuda())
+    dsts = [torch.empty_like(s) for s in srcs]
+    return srcs, dsts, host
+
+
+def time_leg(fsp, plan, srcs, dsts, K, W, world, sampler=None):
+    """W warm-up then K timed solves; returns totals, per-step and per-pass ms."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for i in range(W):
+        plan.solve_into(srcs[i % NSRC], dsts[i % NSRC])
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for row in ev:  # torch creates the CUDA event on first record: create them all now
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t0.record(stream)
+    for i in range(K):
+        plan.set_timing(ev[i])
+        plan.solve_into(srcs[i % NSRC], dsts[i % NSRC])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    plan.set_timing(None)
+    total_ms = t0.elapsed_time(t1)
+    per_pass = np.array([[ev[i][j].elapsed_time(ev[i][j + 1]) for j in range(5)] for i in range(K)])
+    per_step = np.array([ev[i][0].elapsed_time(ev[i][5]) for i in range(K)])
+    return {"total_ms": total_ms, "per_pass": per_pass, "per_step": per_step, "clocks": clocks}
+
+
+def roofline(N, c, r, leg, dtype, hbm, hbm_kind):
+    pb = pass_bytes(N, c, r)
+    share = leg["per_pass"].sum(axis=0)
+    k = int(np.argmax(share))
+    dur_s = float(leg["per_pass"][:, k].mean()) * 1e-3
+    achieved = pb[k] / dur_s / 1e9
+    return {"bound": "hbm", "kernel": PASS_NAMES[k], "achieved": round(achieved, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_kind": hbm_kind + " copy bandwidth",
+            "traffic": recorded_traffic(dtype, N, k), "algorithmic_bytes": int(pb[k]),
+            "pass_ms": [round(float(x), 4) for x in leg["per_pass"].mean(axis=0)],
+            "pass_share": [round(float(x), 4) for x in share / share.sum()]}
+
+
+def e2e_leg(fsp, plan, host_src, dtype, K, W):
+    import torch
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    hin = torch.from_numpy(host_src.astype(np.float32 if dtype == "f32" else np.float64)).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(W):
+        plan.solve_host(hin, hout)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(K):
+        plan.solve_host(hin, hout)
+    dt = time.perf_counter() - t
+    nbytes = hin.numel() * hin.element_size()
+    return {"value": round(K / dt, 2), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": K, "dtype": str(tdt).replace("torch.", ""),
+            "path": "fsp_solve_host: pinned host rho -> device, solve, device -> pinned host phi, per step"}
+
+
+def cpu_oracle(N, L, rho, budget_s=None, max_solves=1):
+    """Oracle T (untimed) then timed full FFT solves on the host cores."""
+    import oracle
+    T = oracle.kernel_T("vg_dct", N, L)
+    times, phi = [], None
+    t_start = time.perf_counter()
+    while len(times) < max_solves:
+        t = time.perf_counter()
+        phi = oracle.solve_fft(T, rho, L / N)
+        times.append(time.perf_counter() - t)
+        if budget_s is not None and time.perf_counter() - t_start + times[-1] > budget_s:
+            break
+    return phi, times, oracle.num_threads()
+
+
+def e_max(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / np.max(np.abs(b)))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    N, L = args.n, 1.0
+    rho = I.gaussian_mixture(N, seed=2405).astype(np.float32).astype(np.float64)
+    import oracle
+    T = oracle.kernel_T("vg_dct", N, L)
+    for _ in range(min(args.warmup, 1)):
+        oracle.solve_fft(T, rho, L / N)
+    t_start = time.perf_counter()
+    times = []
+    while len(times) < args.steps:
+        t = time.perf_counter()
+        oracle.solve_fft(T, rho, L / N)
+        times.append(time.perf_counter() - t)
+        if time.perf_counter() - t_start + times[-1] > args.ref_budget_s:
+            break
+    total = float(sum(times))
+    value = len(times) / total
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "solves/s",
+           "n_gpus": args.gpus, "steps": len(times), "requested_steps": args.steps,
+           "warmup": min(args.warmup, 1), "ms_per_step": round(1e3 * total / len(times), 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic: seeded 8-Gaussian mixture (seed 2405), float32-rounded",
+           "config": {"workload": "VG free-space solve, N=%d^3, unit cube, spectrum precomputed" % N,
+                      "N": N, "L": L, "algo": args.algo},
+           "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": oracle.num_threads(),
+                            "kind": "oracle",
+                            "sample": "%d full N=%d solves (textbook FFT on the full (2N)^3 complex grid), "
+                                      "bounded to ~%.0f s" % (len(times), N, args.ref_budget_s)},
+           "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2405_02603_gb300 as fsp
+    fsp.lib()
+    N, L, K, W = args.n, 1.0, args.steps, max(3, args.warmup)
+    hbm, hbm_kind = measured_peaks()
+
+    legs = {}
+    for dtype in ("f32", "f64"):
+        plan = fsp.Plan(N, L, args.algo, dtype)
+        srcs, dsts, host = make_sources(N, dtype)
+        k = K if dtype == "f32" else max(10, K // 10)
+        sampler = ClockSampler(local) if dtype == "f32" else None
+        leg = time_leg(fsp, plan, srcs, dsts, k, W, world, sampler)
+        leg["K"] = k
+        leg["precompute_ms"] = plan.precompute_ms
+        leg["plan_bytes"] = plan.bytes
+        leg["phi0"] = dsts[0].double().cpu().numpy() if rank == 0 else None
+        leg["e2e"] = e2e_leg(fsp, plan, host[0], dtype, max(20, k // 10), 3) if dtype == "f32" else None
+        leg["tmax_ms"] = max_over_ranks(leg["total_ms"], world)
+        legs[dtype] = leg
+        host0 = host[0]
+        plan.close()
+        del srcs, dsts
+        torch.cuda.empty_cache()
+
+    f32, f64 = legs["f32"], legs["f64"]
+    out = {"metric": METRIC, "value": round(world * f32["K"] / (f32["tmax_ms"] * 1e-3), 2), "unit": "solves/s",
+           "n_gpus": world, "steps": f32["K"], "warmup": W, "ms_per_step": round(f32["tmax_ms"] / f32["K"], 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic: seeded 8-Gaussian mixtures (seeds 2405-2408), float32-rounded, no dataset",
+           "config": {"workload": "VG free-space solve (Sec. 2.2 steps 1-5, Vico-Greengard spectrum), N=%d^3 "
+                                  "cell-centred, unit cube" % N,
+                      "N": N, "L": L, "algo": args.algo, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs rotate over %d source/output pairs; each solve streams ~%.2f GB, > 129 MB L2"
+                            % (NSRC, sum(pass_bytes(N, 8, 4)) / 1e9)},
+           "p50_ms": round(float(np.percentile(f32["per_step"], 50)), 4),
+           "p99_ms": round(float(np.percentile(f32["per_step"], 99)), 4),
+           "hbm_gbs_solve": round(sum(pass_bytes(N, 8, 4)) / (f32["tmax_ms"] / f32["K"] * 1e-3) / 1e9, 1),
+           "roofline": roofline(N, 8, 4, f32, "f32", hbm, hbm_kind),
+           "precompute_ms": round(f32["precompute_ms"], 1), "plan_bytes": f32["plan_bytes"],
+           "gpu_launches": 5 * f32["K"], "clocks": f32["clocks"], "e2e": f32["e2e"]}
+    t64 = f64["tmax_ms"] / f64["K"]
+    out["fp64"] = {"value": round(world * f64["K"] / (f64["tmax_ms"] * 1e-3), 2), "unit": "solves/s",
+                   "steps": f64["K"], "ms_per_step": round(t64, 4),
+                   "p50_ms": round(float(np.percentile(f64["per_step"], 50)), 4),
+                   "p99_ms": round(float(np.percentile(f64["per_step"], 99)), 4),
+                   "hbm_gbs_solve": round(sum(pass_bytes(N, 16, 8)) / (t64 * 1e-3) / 1e9, 1),
+                   "roofline": roofline(N, 16, 8, f64, "f64", hbm, hbm_kind),
+                   "nominal_gflops": round(solve_flops(N) / (t64 * 1e-3) / 1e9, 1),
+                   "precompute_ms": round(f64["precompute_ms"], 1), "gpu_launches": 5 * f64["K"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        phi_ref, times, cores = cpu_oracle(N, L, host0)
+        out["cpu_baseline"] = {"value": round(1.0 / float(np.mean(times)), 5), "unit": "solves/s",
+                               "cores": cores, "kind": "oracle",
+                               "sample": "%d full N=%d VG solve(s) of source 0 (oracle: textbook FFT on the "
+                                         "full (2N)^3 complex grid, spectrum precomputed untimed)"
+                                         % (len(times), N)}
+        out["e_max_vs_oracle"] = {"f32": e_max(f32["phi0"], phi_ref), "f64": e_max(f64["phi0"], phi_ref)}
+        out["fp64"]["e_max_vs_oracle"] = out["e_max_vs_oracle"]["f64"]
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

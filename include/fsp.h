@@ -1,0 +1,173 @@
+/*
+ * fsp.h -- C ABI of the GB300 (sm_103a) free-space spectral Poisson solver.
+ *
+ * The solver computes the free-space potential of a source sampled on an N^3
+ * cell-centred grid of spacing h (cube side L = N h), the convolution
+ * phi = G * rho with G(x) = 1/(4 pi |x|) (Sec. 1, Eq. convolution_eq of
+ * Mayani et al., arXiv 2405.02603, with eps0 = 1), by the Hockney-Eastwood
+ * doubled-grid FFT convolution (Sec. 2.2, steps 1-5):
+ *
+ *   phi_i = h^3 sum_{j in [0,N)^3} T[|i - j|] rho_j ,   i in [0,N)^3,
+ *
+ * where T is the real-space kernel of the chosen method (fsp_algo):
+ *   FSP_HE     Hockney-Eastwood: T[m] = 1/(4 pi h |m|), T[0] = 1/(4 pi)
+ *              (Sec. 2.2 step 3; origin value in this sign convention).
+ *   FSP_VG     Vico-Greengard: inverse DFT on the (4N)^3 grid of the truncated
+ *              spectral kernel G_L(k) = 2 (sin(L_t|k|/2)/|k|)^2 (Sec. 2.3, Eq.
+ *              green_vico), L_t = 1.1 sqrt(3) L, restricted to the doubled grid.
+ *   FSP_VG_DCT the paper's memory-reduced variant: the same kernel from a DCT-I
+ *              on (2N+1)^3 samples (Sec. 2.4).
+ *
+ * Arrays: rho and phi are dense C-order arrays of N^3 reals, index
+ * (z*N + y)*N + x, x fastest; `double` for FSP_F64, `float` for
+ * FSP_F32_MIXED.  They belong to the caller.  phi == rho (in place) is allowed.
+ *
+ * Streams: `fsp_stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Device work is enqueued asynchronously on the given stream; an asynchronous
+ * CUDA fault surfaces as FSP_ECUDA from a later call or from fsp_plan_sync.
+ *
+ * Errors: every entry point returns an fsp_status and never aborts the
+ * process.  Arguments are validated synchronously before any device work is
+ * enqueued; on an error return nothing has been enqueued and no output or
+ * plan state has changed unless stated otherwise.
+ */
+#ifndef FSP_H
+#define FSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fsp_stream; /* identical to cudaStream_t */
+
+typedef enum {
+    FSP_OK = 0,
+    FSP_EINVAL = 1,       /* bad argument, NULL or misaligned pointer, unknown or destroyed plan */
+    FSP_EUNSUPPORTED = 2, /* size outside what the kernels support (e.g. 2N not 2/3/5-smooth) */
+    FSP_ENOMEM = 3,       /* device allocation failed or exceeded a memory budget */
+    FSP_ECUDA = 4,        /* a CUDA runtime call or a kernel launch failed */
+    FSP_EBUSY = 5,        /* a queue or slot limit is reached; retry later */
+    FSP_ETIMEOUT = 6      /* a bounded device-side wait ran out */
+} fsp_status;
+
+/* The paper's solver names HOCKNEY, VICO and VICO_2 (Sec. 4, availability). */
+typedef enum { FSP_HE = 0, FSP_VG = 1, FSP_VG_DCT = 2 } fsp_algo;
+
+/* FSP_F64: every step in double precision.
+ * FSP_F32_MIXED: the solve (all transforms and the spectral multiply) in
+ * single precision; the Green's spectrum is precomputed in double precision
+ * and rounded once to single precision. */
+typedef enum { FSP_F64 = 0, FSP_F32_MIXED = 1 } fsp_dtype;
+
+typedef struct fsp_plan fsp_plan;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *fsp_status_str(fsp_status s);
+
+/*
+ * fsp_plan_create -- build a solver for one (N, L, h, algo, dtype) on the
+ * current CUDA device.
+ *
+ * N      grid points per axis, N >= 2; 2N must be 2/3/5-smooth, and 4N too for
+ *        FSP_VG (otherwise FSP_EUNSUPPORTED); N <= 1024.
+ * L      cube side, L > 0 and finite.
+ * h      grid spacing; must equal L/N to 1e-12 relative (else FSP_EINVAL).
+ * algo   FSP_HE, FSP_VG or FSP_VG_DCT.
+ * dtype  FSP_F64 or FSP_F32_MIXED.
+ * stream the precompute (plan-time Green's spectrum, Sec. 2.2 step 3, Sec. 2.3
+ *        and Sec. 2.4) runs on this stream; the call returns after it has
+ *        completed (it synchronises the stream) and temporaries are freed.
+ *
+ * The plan owns the spectrum S ((N+1)^3 reals) and the solve workspace
+ * (3 N^2 P complex values, P = N+1 rounded up to 16).  FSP_VG needs a
+ * (4N)^3 complex FP64 temporary, FSP_VG_DCT a (2N+1)^3 FP64 one, during the
+ * call only.  On failure *out is set to NULL and nothing is leaked.
+ */
+fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo algo, fsp_dtype dtype,
+                           fsp_stream stream);
+
+/*
+ * fsp_solve -- one free-space solve, phi = G * rho (Sec. 2.2 steps 1-5):
+ * zero-pad to (2N)^3 (never materialised), 3D real-to-complex FFT, multiply
+ * by the plan's spectrum, inverse FFT, restrict to N^3.  Five kernel launches
+ * on `stream`, asynchronous.
+ *
+ * rho, phi: DEVICE pointers on the plan's device, 16-byte aligned, N^3 reals
+ * of the plan's dtype; phi == rho allowed, other overlaps are not.  One solve
+ * per plan may be in flight at a time (the workspace is per plan): solves on
+ * one stream serialise naturally; concurrent streams need separate plans.
+ */
+fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stream);
+
+/*
+ * fsp_solve_host -- the same solve on HOST arrays: copies rho host->device,
+ * solves, copies phi device->host, all on `stream`, and returns after the
+ * stream has completed the copy back.  rho/phi: host pointers (pinned memory
+ * gives asynchronous, full-bandwidth copies), N^3 reals of the plan's dtype.
+ * The first call allocates two N^3 device staging buffers kept by the plan.
+ */
+fsp_status fsp_solve_host(fsp_plan *plan, const void *rho_host, void *phi_host, fsp_stream stream);
+
+/* Wait for all work enqueued for this plan's solves and report any
+ * asynchronous CUDA error as FSP_ECUDA. */
+fsp_status fsp_plan_sync(fsp_plan *plan, fsp_stream stream);
+
+/* Release the plan and all its device memory.  Waits for the device first.
+ * A destroyed or unknown pointer returns FSP_EINVAL (plans are tracked in a
+ * registry, so a stale pointer is detected instead of dereferenced). */
+fsp_status fsp_plan_destroy(fsp_plan *plan);
+
+/*
+ * fsp_plan_set_timing -- per-pass timing hook.  With nevents == 6, every later
+ * fsp_solve on this plan records events[i] on the solve's stream just before
+ * pass i (i = 0..4: pad+x-R2C, y-FFT, z-FFT*S*z-IFFT, y-IFFT, x-C2R) and
+ * events[5] after the last pass, so that each kernel can be timed on the
+ * stream it runs on.  events are cudaEvent_t handles owned by the caller
+ * (created and destroyed by it, on the plan's device); nevents == 0 (events
+ * may be NULL) turns the hook off.  Any other count returns FSP_EINVAL.
+ */
+fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents);
+
+/* Device bytes the plan holds (spectrum + workspace + tables), 0 if invalid. */
+size_t fsp_plan_bytes(const fsp_plan *plan);
+
+/* Wall time of the plan-time precompute in milliseconds, < 0 if invalid. */
+double fsp_plan_precompute_ms(const fsp_plan *plan);
+
+/*
+ * fsp_plan_spectrum -- copy the plan's multiplier to host memory as doubles:
+ * S[q] = h^3 DFT_{2N}{G_2}[q] / (2N)^3 for q in [0,N]^3, shape (N+1)^3,
+ * index (qz*(N+1) + qy)*(N+1) + qx (the spectrum of the mirrored kernel is
+ * real and even per axis, so this octant holds all of it).  For
+ * FSP_F32_MIXED the values are the single-precision ones the solve uses.
+ * Synchronous.  s_host must hold (N+1)^3 doubles.
+ */
+fsp_status fsp_plan_spectrum(const fsp_plan *plan, double *s_host);
+
+/*
+ * fsp_kernel_T -- the real-space kernel T[m], m in [0,N]^3, of `algo`
+ * (Sec. 2.2 step 3, Sec. 2.3, Sec. 2.4), computed on the current device in
+ * FP64 exactly as fsp_plan_create computes it, written to the DEVICE array
+ * t_dev ((N+1)^3 doubles, index (mz*(N+1)+my)*(N+1)+mx).  Same size rules as
+ * fsp_plan_create.  Synchronises `stream`; temporaries are freed.
+ */
+fsp_status fsp_kernel_T(int N, double L, fsp_algo algo, double *t_dev, fsp_stream stream);
+
+/*
+ * fsp_fft_c2c -- `count` independent unnormalised 1D FFTs of length n
+ * (2/3/5-smooth, 1 <= n <= 4096) with the solver's line kernels:
+ * X[k] = sum_j x[j] exp(sign 2 pi i jk / n), sign = -1 (forward) or +1.
+ * in/out: DEVICE arrays of count*n interleaved complex values (re, im),
+ * contiguous lines, `double` (dtype FSP_F64) or `float` (FSP_F32_MIXED);
+ * in == out allowed.  Asynchronous on `stream`.
+ */
+fsp_status fsp_fft_c2c(int n, int count, fsp_dtype dtype, int sign, const void *in, void *out, fsp_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSP_H */

@@ -1,0 +1,205 @@
+"""Python binding of libfsp.so, the GB300 free-space spectral Poisson solver.
+
+Thin ctypes marshalling over the C ABI declared in include/fsp.h: every step of
+every solve runs in the library's CUDA kernels.  PyTorch is used only to own
+device memory (``tensor.data_ptr()``) and to name streams
+(``torch.cuda.current_stream().cuda_stream``).  There is no CPU fallback: if
+the library is missing or a call fails, an exception is raised.
+
+    import torch, paper_2405_02603_gb300 as fsp
+    plan = fsp.Plan(N=256, L=1.0, algo="vg_dct", dtype="f32")
+    phi = plan.solve(rho)          # rho: CUDA tensor (N, N, N) float32
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+FSP_OK, FSP_EINVAL, FSP_EUNSUPPORTED, FSP_ENOMEM, FSP_ECUDA, FSP_EBUSY, FSP_ETIMEOUT = range(7)
+STATUS_NAMES = ["FSP_OK", "FSP_EINVAL", "FSP_EUNSUPPORTED", "FSP_ENOMEM", "FSP_ECUDA", "FSP_EBUSY",
+                "FSP_ETIMEOUT"]
+ALGOS = {"he": 0, "vg": 1, "vg_dct": 2}
+DTYPES = {"f64": 0, "f32": 1}
+
+_lib = None
+
+
+class FspError(RuntimeError):
+    """A non-FSP_OK status returned by the library."""
+
+    def __init__(self, status, where=""):
+        self.status = int(status)
+        name = STATUS_NAMES[self.status] if 0 <= self.status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s%s" % (where + ": " if where else "", name))
+
+
+def library_path():
+    return _build.library_path()
+
+
+def lib(build_if_missing=True):
+    """Load libfsp.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.library_path()
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise FspError(FSP_ECUDA, "libfsp.so not built (" + path + ")")
+    L = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    L.fsp_status_str.restype = ctypes.c_char_p
+    L.fsp_status_str.argtypes = [i]
+    L.fsp_plan_create.argtypes = [ctypes.POINTER(vp), i, d, d, i, i, vp]
+    L.fsp_solve.argtypes = [vp, vp, vp, vp]
+    L.fsp_solve_host.argtypes = [vp, vp, vp, vp]
+    L.fsp_plan_sync.argtypes = [vp, vp]
+    L.fsp_plan_destroy.argtypes = [vp]
+    L.fsp_plan_bytes.argtypes = [vp]
+    L.fsp_plan_bytes.restype = sz
+    L.fsp_plan_precompute_ms.argtypes = [vp]
+    L.fsp_plan_precompute_ms.restype = d
+    L.fsp_plan_spectrum.argtypes = [vp, vp]
+    L.fsp_kernel_T.argtypes = [i, d, i, vp, vp]
+    L.fsp_fft_c2c.argtypes = [i, i, i, i, vp, vp, vp]
+    L.fsp_plan_set_timing.argtypes = [vp, ctypes.POINTER(vp), i]
+    for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
+                 "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c"):
+        getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+def check(status, where=""):
+    if status != FSP_OK:
+        raise FspError(status, where)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(dtype):
+    return DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+
+
+def _algo_code(algo):
+    return ALGOS[algo] if isinstance(algo, str) else int(algo)
+
+
+def torch_dtype(dtype):
+    import torch
+    return torch.float64 if _dtype_code(dtype) == 0 else torch.float32
+
+
+class Plan:
+    """One solver instance for (N, L, algo, dtype): fsp_plan_create / fsp_solve / fsp_plan_destroy."""
+
+    def __init__(self, N, L=1.0, algo="vg_dct", dtype="f64", h=None, stream=None):
+        self.N, self.L = int(N), float(L)
+        self.algo, self.dtype = algo, dtype
+        self.h = self.L / self.N if h is None else float(h)
+        self._p = ctypes.c_void_p()
+        check(lib().fsp_plan_create(ctypes.byref(self._p), self.N, self.L, self.h, _algo_code(algo),
+                                    _dtype_code(dtype), _stream_handle(stream)), "fsp_plan_create")
+
+    @property
+    def handle(self):
+        return self._p
+
+    @property
+    def bytes(self):
+        return int(lib().fsp_plan_bytes(self._p))
+
+    @property
+    def precompute_ms(self):
+        return float(lib().fsp_plan_precompute_ms(self._p))
+
+    def solve_into(self, rho, phi, stream=None):
+        """Enqueue phi = G * rho on the stream (both CUDA tensors, contiguous)."""
+        self._check_tensor(rho)
+        self._check_tensor(phi)
+        check(lib().fsp_solve(self._p, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                              _stream_handle(stream)), "fsp_solve")
+        return phi
+
+    def solve(self, rho, stream=None):
+        import torch
+        phi = torch.empty_like(rho)
+        return self.solve_into(rho, phi, stream)
+
+    def solve_host(self, rho_host, phi_host, stream=None):
+        """Host arrays (numpy or CPU tensors, ideally pinned): copy in, solve, copy out."""
+        rp = rho_host.data_ptr() if hasattr(rho_host, "data_ptr") else rho_host.ctypes.data
+        pp = phi_host.data_ptr() if hasattr(phi_host, "data_ptr") else phi_host.ctypes.data
+        check(lib().fsp_solve_host(self._p, ctypes.c_void_p(rp), ctypes.c_void_p(pp), _stream_handle(stream)),
+              "fsp_solve_host")
+        return phi_host
+
+    def spectrum(self):
+        import numpy as np
+        out = np.empty((self.N + 1,) * 3, dtype=np.float64)
+        check(lib().fsp_plan_spectrum(self._p, ctypes.c_void_p(out.ctypes.data)), "fsp_plan_spectrum")
+        return out
+
+    def set_timing(self, events):
+        """Record the 6 torch.cuda.Event objects around the 5 passes of each
+        later solve (None turns the hook off)."""
+        if events is None:
+            check(lib().fsp_plan_set_timing(self._p, None, 0), "fsp_plan_set_timing")
+            self._events = None
+            return
+        self._events = list(events)  # keep them alive while the hook is set
+        arr = (ctypes.c_void_p * 6)(*[ctypes.c_void_p(e.cuda_event) for e in self._events])
+        check(lib().fsp_plan_set_timing(self._p, arr, 6), "fsp_plan_set_timing")
+
+    def sync(self, stream=None):
+        check(lib().fsp_plan_sync(self._p, _stream_handle(stream)), "fsp_plan_sync")
+
+    def close(self):
+        if self._p is not None and self._p.value:
+            check(lib().fsp_plan_destroy(self._p), "fsp_plan_destroy")
+        self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_tensor(self, t):
+        import torch
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch_dtype(self.dtype) and t.numel() == self.N ** 3):
+            raise FspError(FSP_EINVAL, "tensor must be a contiguous CUDA %s tensor of N^3 elements"
+                           % torch_dtype(self.dtype))
+
+
+def kernel_T(N, L=1.0, algo="vg_dct", stream=None):
+    """The FP64 real-space kernel T[m], m in [0,N]^3, computed on the device."""
+    import torch
+    t = torch.empty((N + 1,) * 3, dtype=torch.float64, device="cuda")
+    check(lib().fsp_kernel_T(int(N), float(L), _algo_code(algo), ctypes.c_void_p(t.data_ptr()),
+                             _stream_handle(stream)), "fsp_kernel_T")
+    return t
+
+
+def fft_c2c(x, sign=-1, stream=None):
+    """Batched 1D FFTs along the last axis of a complex CUDA tensor (library kernels)."""
+    import torch
+    x = x.contiguous()
+    dtype = 0 if x.dtype == torch.complex128 else 1
+    if x.dtype not in (torch.complex128, torch.complex64):
+        raise FspError(FSP_EINVAL, "fft_c2c wants complex64 or complex128")
+    out = torch.empty_like(x)
+    n = x.shape[-1]
+    count = x.numel() // n if n else 0
+    check(lib().fsp_fft_c2c(n, count, dtype, int(sign), ctypes.c_void_p(x.data_ptr()),
+                            ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "fsp_fft_c2c")
+    return out
+
+
+__all__ = ["Plan", "FspError", "kernel_T", "fft_c2c", "lib", "check", "library_path", "ALGOS", "DTYPES"]

@@ -1,0 +1,556 @@
+// api.cu -- the C ABI of include/fsp.h: plan registry, argument validation,
+// the plan-time Green's spectrum pipeline and the five-pass solve.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <unordered_set>
+
+#include "../../include/fsp.h"
+#include "greens.h"
+#include "kernels.cuh"
+
+using namespace fsp;
+
+namespace {
+
+constexpr uint64_t kMagic = 0x46535050'4c414e31ULL;  // "FSPPLAN1"
+constexpr int kMaxN = 1024;
+constexpr double kAlpha = 1.1;  // Vico-Greengard window factor (Sec. 2.3)
+
+std::mutex g_mu;
+std::unordered_set<const fsp_plan *> g_plans;
+
+bool is_235_smooth(long long n) {
+    if (n < 1) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Radix schedule: 5s, then 3s, then 8s, then one 4 or 2.
+bool make_stages(int n, Stages &st) {
+    std::memset(&st, 0, sizeof(st));
+    st.n = n;
+    int m = n;
+    while (m % 5 == 0) m /= 5, ++st.n5;
+    while (m % 3 == 0) m /= 3, ++st.n3;
+    while (m % 8 == 0) m /= 8, ++st.n8;
+    if (m % 4 == 0) m /= 4, st.last = 4;
+    else if (m % 2 == 0) m /= 2, st.last = 2;
+    return m == 1;
+}
+
+// Smallest threads-per-line (>= n/16) for which every stage keeps at most
+// kMaxV complex values per thread.
+int threads_per_line(const Stages &st) {
+    int radices[4] = {st.n5 ? 5 : 0, st.n3 ? 3 : 0, st.n8 ? 8 : 0, st.last};
+    int tpl = st.n / 16;
+    if (tpl < 1) tpl = 1;
+    for (;; ++tpl) {
+        bool ok = true;
+        for (int R : radices) {
+            if (!R) continue;
+            const int nb = st.n / R;
+            const int K = (nb + tpl - 1) / tpl;
+            if (K > kMaxV / R) ok = false;
+        }
+        if (ok) return tpl;
+    }
+}
+
+// Lines per CTA (2^lgL): as many as wanted, within 512 threads and 200 KB of
+// shared memory (positions x (L+1) complex elements).
+bool choose_tile(int positions, int tpl, size_t csize, int want_lgL, int &lgL) {
+    for (lgL = want_lgL; lgL >= 0; --lgL) {
+        const int L = 1 << lgL;
+        const size_t sm = (size_t)positions * (L + 1) * csize;
+        if (L * tpl <= 512 && sm <= 200 * 1024) return true;
+    }
+    return false;
+}
+
+struct TileCfg {
+    Stages st;
+    int tpl = 0, lgL = 0;
+};
+
+bool make_cfg(int n, int positions, size_t csize, int want_lgL, TileCfg &c) {
+    if (!make_stages(n, c.st)) return false;
+    c.tpl = threads_per_line(c.st);
+    return choose_tile(positions, c.tpl, csize, want_lgL, c.lgL);
+}
+
+fsp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FSP_OK : FSP_ECUDA; }
+
+#define FSP_TRY_CUDA(expr)                              \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return FSP_ECUDA;        \
+    } while (0)
+
+// Device memory owned by one scope: freed on every exit path.
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes); }
+    void *release() {
+        void *q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+fsp_status alloc_or_nomem(DevBuf &b, size_t bytes) {
+    cudaError_t e = b.alloc(bytes);
+    if (e == cudaSuccess) return FSP_OK;
+    cudaGetLastError();  // clear the sticky-free allocation error
+    return e == cudaErrorMemoryAllocation ? FSP_ENOMEM : FSP_ECUDA;
+}
+
+// FP64 forward-roots table of length n in a scope-owned buffer.
+fsp_status roots_f64(DevBuf &b, int n, cudaStream_t s) {
+    fsp_status st = alloc_or_nomem(b, sizeof(double2) * (size_t)n);
+    if (st != FSP_OK) return st;
+    return cuda_status(launch_roots<double>(b.p, n, s));
+}
+
+// -------------------------------------------------------- plan-time kernels
+// Real-space kernel T[m], m in [0,N]^3, into t_dev (FP64).  Asynchronous on s;
+// temporaries are owned by `keep` and must outlive the enqueued work.
+struct Temps {
+    DevBuf g, a1, a2, tw;
+};
+
+fsp_status enqueue_kernel_T(int N, double L, fsp_algo algo, double *t_dev, cudaStream_t s, Temps &tmp) {
+    const double h = L / N;
+    const int k1 = N + 1;
+    const double Lt = kAlpha * std::sqrt(3.0) * L;
+    fsp_status st;
+    if (algo == FSP_HE) return cuda_status(launch_he_T(t_dev, N, h, s));
+
+    const double scale = 1.0 / ((4.0 * N * h) * (4.0 * N * h) * (4.0 * N * h));
+    if (algo == FSP_VG_DCT) {
+        // Sec. 2.4: G_L on [0,2N]^3, DCT-I per axis (M = 2N, even extension to
+        // 4N), keeping outputs [0,N] of each axis, then (4Nh)^-3.
+        const int M = 2 * N, nm = M + 1, n = 2 * M;
+        TileCfg cr, cc;
+        if (!make_cfg(n, n, sizeof(double2), 3, cr) || !make_cfg(n, n, sizeof(double2), 3, cc)) return FSP_EUNSUPPORTED;
+        if ((st = alloc_or_nomem(tmp.g, sizeof(double) * (size_t)nm * nm * nm)) != FSP_OK) return st;
+        if ((st = alloc_or_nomem(tmp.a1, sizeof(double) * (size_t)nm * nm * k1)) != FSP_OK) return st;
+        if ((st = alloc_or_nomem(tmp.a2, sizeof(double) * (size_t)nm * k1 * k1)) != FSP_OK) return st;
+        if ((st = roots_f64(tmp.tw, n, s)) != FSP_OK) return st;
+        FSP_TRY_CUDA(launch_vg_sample_octant((double *)tmp.g.p, N, h, Lt, s));
+        LinesArgs a{};
+        a.tw = tmp.tw.p;
+        a.st = cr.st;
+        a.tpl = cr.tpl;
+        a.lgL = cr.lgL;
+        // x: rows of M+1 reals -> rows of N+1
+        a.in = tmp.g.p;
+        a.out = tmp.a1.p;
+        a.in_pos = 1, a.in_line = nm, a.in_batch = 0;
+        a.out_pos = 1, a.out_line = k1, a.out_batch = 0;
+        a.n_out = k1, a.nlines = nm * nm, a.nbatch = 1;
+        FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+        // y: columns (x in [0,N]) of a1[z][y][x]
+        a.tpl = cc.tpl, a.lgL = cc.lgL;
+        a.in = tmp.a1.p;
+        a.out = tmp.a2.p;
+        a.in_pos = k1, a.in_line = 1, a.in_batch = (long long)nm * k1;
+        a.out_pos = k1, a.out_line = 1, a.out_batch = (long long)k1 * k1;
+        a.n_out = k1, a.nlines = k1, a.nbatch = nm;
+        FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+        // z: columns of a2[z][y][x], batch y
+        a.in = tmp.a2.p;
+        a.out = t_dev;
+        a.in_pos = (long long)k1 * k1, a.in_line = 1, a.in_batch = k1;
+        a.out_pos = (long long)k1 * k1, a.out_line = 1, a.out_batch = k1;
+        a.n_out = k1, a.nlines = k1, a.nbatch = k1;
+        FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+        return cuda_status(launch_scale(t_dev, (long long)k1 * k1 * k1, scale, s));
+    }
+    // FSP_VG, Sec. 2.3: G_L on the (4N)^3 grid, unnormalised inverse DFT per
+    // axis, restricted to [0,N] per axis, real part, times (4Nh)^-3.
+    const int n4 = 4 * N;
+    TileCfg cr, cc;
+    if (!make_cfg(n4, n4, sizeof(double2), 3, cr) || !make_cfg(n4, n4, sizeof(double2), 3, cc)) return FSP_EUNSUPPORTED;
+    if ((st = alloc_or_nomem(tmp.g, sizeof(double2) * (size_t)n4 * n4 * n4)) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(tmp.a1, sizeof(double2) * (size_t)n4 * n4 * k1)) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(tmp.a2, sizeof(double2) * (size_t)n4 * k1 * k1)) != FSP_OK) return st;
+    if ((st = roots_f64(tmp.tw, n4, s)) != FSP_OK) return st;
+    FSP_TRY_CUDA(launch_vg_sample_full(tmp.g.p, N, h, Lt, s));
+    LinesArgs a{};
+    a.tw = tmp.tw.p;
+    a.st = cr.st, a.tpl = cr.tpl, a.lgL = cr.lgL;
+    a.in = tmp.g.p, a.out = tmp.a1.p;
+    a.in_pos = 1, a.in_line = n4, a.in_batch = 0;
+    a.out_pos = 1, a.out_line = k1, a.out_batch = 0;
+    a.n_in = n4, a.n_out = k1, a.nlines = n4 * n4, a.nbatch = 1;
+    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_CPLX, M_INV>(a, s)));
+    a.tpl = cc.tpl, a.lgL = cc.lgL;
+    a.in = tmp.a1.p, a.out = tmp.a2.p;
+    a.in_pos = k1, a.in_line = 1, a.in_batch = (long long)n4 * k1;
+    a.out_pos = k1, a.out_line = 1, a.out_batch = (long long)k1 * k1;
+    a.n_in = n4, a.n_out = k1, a.nlines = k1, a.nbatch = n4;
+    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_CPLX, M_INV>(a, s)));
+    a.in = tmp.a2.p, a.out = t_dev;
+    a.in_pos = (long long)k1 * k1, a.in_line = 1, a.in_batch = k1;
+    a.out_pos = (long long)k1 * k1, a.out_line = 1, a.out_batch = k1;
+    a.n_in = n4, a.n_out = k1, a.nlines = k1, a.nbatch = k1;
+    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_REAL, M_INV>(a, s)));
+    return cuda_status(launch_scale(t_dev, (long long)k1 * k1 * k1, scale, s));
+}
+
+// Spectrum of the mirrored kernel: DCT-I of length N+1 per axis on T in place
+// (the 2N DFT of a real sequence even about 0 and N), FP64.
+fsp_status enqueue_dct_spectrum(int N, double *t_dev, cudaStream_t s, DevBuf &tw) {
+    const int k1 = N + 1, n = 2 * N;
+    TileCfg c;
+    if (!make_cfg(n, n, sizeof(double2), 3, c)) return FSP_EUNSUPPORTED;
+    fsp_status st = roots_f64(tw, n, s);
+    if (st != FSP_OK) return st;
+    LinesArgs a{};
+    a.tw = tw.p, a.st = c.st, a.tpl = c.tpl, a.lgL = c.lgL;
+    a.in = a.out = t_dev;
+    a.n_out = k1;
+    // x: rows
+    a.in_pos = a.out_pos = 1, a.in_line = a.out_line = k1, a.in_batch = a.out_batch = 0;
+    a.nlines = k1 * k1, a.nbatch = 1;
+    FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+    // y: columns, batch z
+    a.in_pos = a.out_pos = k1, a.in_line = a.out_line = 1, a.in_batch = a.out_batch = (long long)k1 * k1;
+    a.nlines = k1, a.nbatch = k1;
+    FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+    // z: columns, batch y
+    a.in_pos = a.out_pos = (long long)k1 * k1, a.in_batch = a.out_batch = k1;
+    FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+    return FSP_OK;
+}
+
+fsp_status validate_size(int N, double L, fsp_algo algo) {
+    if (N < 2 || N > kMaxN) return N < 2 ? FSP_EINVAL : FSP_EUNSUPPORTED;
+    if (!(L > 0.0) || !std::isfinite(L)) return FSP_EINVAL;
+    if (algo != FSP_HE && algo != FSP_VG && algo != FSP_VG_DCT) return FSP_EINVAL;
+    if (!is_235_smooth(2LL * N)) return FSP_EUNSUPPORTED;
+    if (algo == FSP_VG && !is_235_smooth(4LL * N)) return FSP_EUNSUPPORTED;
+    return FSP_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan --
+struct fsp_plan {
+    uint64_t magic = 0;
+    int N = 0, P = 0, device = 0;
+    double L = 0, h = 0;
+    fsp_algo algo = FSP_HE;
+    fsp_dtype dtype = FSP_F64;
+    size_t rsize = 8;  // bytes per real
+    void *S = nullptr, *W1 = nullptr, *W2 = nullptr, *tw_n = nullptr, *tw_2n = nullptr;
+    void *stage_rho = nullptr, *stage_phi = nullptr;
+    TileCfg row, col;
+    cudaEvent_t ev[6] = {};
+    bool timing = false;
+    size_t bytes = 0;
+    double precompute_ms = 0;
+};
+
+namespace {
+
+bool plan_live(const fsp_plan *p) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return p && g_plans.count(p) && p->magic == kMagic;
+}
+
+void plan_free(fsp_plan *p) {
+    for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi})
+        if (q) cudaFree(q);
+    p->magic = 0;
+    delete p;
+}
+
+template <typename T> cudaError_t enqueue_solve(const fsp_plan *p, const void *rho, void *phi, cudaStream_t s) {
+    const int N = p->N;
+    const long long P = p->P;
+    cudaError_t e;
+    auto mark = [&](int i) { return p->timing ? cudaEventRecord(p->ev[i], s) : cudaSuccess; };
+    // P1: pad + x-R2C (rows of rho -> W1[z][y][kx])
+    if ((e = mark(0)) != cudaSuccess) return e;
+    RowsArgs r{};
+    r.x = rho, r.c = p->W1, r.x_row = N, r.c_row = P, r.N = N, r.nrows = N * N;
+    r.lgL = p->row.lgL, r.tpl = p->row.tpl, r.st = p->row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    if ((e = launch_r2c_rows<T>(r, s)) != cudaSuccess) return e;
+    if ((e = mark(1)) != cudaSuccess) return e;
+    // P2: y-FFT (columns kx of W1[z][y][.], y < N zero-padded to 2N) -> W2[z][ky][kx]
+    LinesArgs a{};
+    a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_2n;
+    a.in = p->W1, a.out = p->W2;
+    a.in_pos = P, a.in_line = 1, a.in_batch = (long long)N * P;
+    a.out_pos = P, a.out_line = 1, a.out_batch = 2LL * N * P;
+    a.n_in = N, a.n_out = 2 * N, a.nlines = N + 1, a.nbatch = N;
+    if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD>(a, s)) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
+    // P3: z-FFT, multiply by S, z-IFFT, keep z < N (in place in W2, batch ky)
+    a.in = a.out = p->W2;
+    a.in_pos = a.out_pos = 2LL * N * P, a.in_batch = a.out_batch = P;
+    a.n_in = N, a.n_out = N, a.nbatch = 2 * N;
+    a.S = p->S, a.s_pos = (long long)(N + 1) * P, a.s_batch = P, a.half = N;
+    if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD_MUL_INV>(a, s)) != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
+    // P4: y-IFFT, keep y < N: W2[z][ky][kx] -> W1[z][y][kx]
+    a.in = p->W2, a.out = p->W1;
+    a.in_pos = P, a.in_batch = 2LL * N * P;
+    a.out_pos = P, a.out_batch = (long long)N * P;
+    a.n_in = 2 * N, a.n_out = N, a.nbatch = N;
+    if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_INV>(a, s)) != cudaSuccess) return e;
+    if ((e = mark(4)) != cudaSuccess) return e;
+    // P5: x-C2R, keep x < N: W1 rows -> phi
+    r.x = phi;
+    if ((e = launch_c2r_rows<T>(r, s)) != cudaSuccess) return e;
+    return mark(5);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fsp_status_str(fsp_status s) {
+    switch (s) {
+    case FSP_OK: return "FSP_OK";
+    case FSP_EINVAL: return "FSP_EINVAL: invalid argument";
+    case FSP_EUNSUPPORTED: return "FSP_EUNSUPPORTED: unsupported size";
+    case FSP_ENOMEM: return "FSP_ENOMEM: out of device memory or over budget";
+    case FSP_ECUDA: return "FSP_ECUDA: CUDA error";
+    case FSP_EBUSY: return "FSP_EBUSY: busy";
+    case FSP_ETIMEOUT: return "FSP_ETIMEOUT: device-side wait timed out";
+    }
+    return "FSP_?: unknown status";
+}
+
+fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo algo, fsp_dtype dtype,
+                           fsp_stream stream) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    fsp_status st = validate_size(N, L, algo);
+    if (st != FSP_OK) return st;
+    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED) return FSP_EINVAL;
+    if (!(std::fabs(h - L / N) <= 1e-12 * std::fabs(L / N))) return FSP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+
+    fsp_plan *p = new fsp_plan();
+    p->N = N, p->L = L, p->h = L / N, p->algo = algo, p->dtype = dtype;
+    p->rsize = dtype == FSP_F64 ? 8 : 4;
+    p->P = ((N + 1) + 15) / 16 * 16;
+    const size_t csize = 2 * p->rsize;
+    // tiles: rows (length-N FFT, N+1 positions), columns (length 2N)
+    const int row_lgL = dtype == FSP_F64 ? 3 : 4, col_lgL = dtype == FSP_F64 ? 3 : 4;
+    if (!make_cfg(N, N + 1, csize, row_lgL, p->row) || !make_cfg(2 * N, 2 * N, csize, col_lgL, p->col)) {
+        delete p;
+        return FSP_EUNSUPPORTED;
+    }
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return FSP_ECUDA;
+    }
+    auto fail = [&](fsp_status e) {
+        cudaStreamSynchronize(s);
+        plan_free(p);
+        return e;
+    };
+    const size_t k1 = N + 1;
+    const size_t sbytes = k1 * k1 * p->P * p->rsize;
+    const size_t w1 = (size_t)N * N * p->P * csize, w2 = 2 * w1;
+    DevBuf bS, bW1, bW2, bt1, bt2;
+    if ((st = alloc_or_nomem(bS, sbytes)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(bW1, w1)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(bW2, w2)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(bt1, csize * N)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(bt2, csize * 2 * N)) != FSP_OK) return fail(st);
+    p->S = bS.release(), p->W1 = bW1.release(), p->W2 = bW2.release();
+    p->tw_n = bt1.release(), p->tw_2n = bt2.release();
+    p->bytes = sbytes + w1 + w2 + csize * 3 * N;
+    cudaError_t e;
+    if (dtype == FSP_F64) {
+        e = launch_roots<double>(p->tw_n, N, s);
+        if (e == cudaSuccess) e = launch_roots<double>(p->tw_2n, 2 * N, s);
+    } else {
+        e = launch_roots<float>(p->tw_n, N, s);
+        if (e == cudaSuccess) e = launch_roots<float>(p->tw_2n, 2 * N, s);
+    }
+    if (e != cudaSuccess) return fail(FSP_ECUDA);
+
+    {  // plan-time spectrum, FP64 throughout
+        Temps tmp;
+        DevBuf Td, tw;
+        if ((st = alloc_or_nomem(Td, sizeof(double) * k1 * k1 * k1)) != FSP_OK) return fail(st);
+        if ((st = enqueue_kernel_T(N, L, algo, (double *)Td.p, s, tmp)) != FSP_OK) return fail(st);
+        if ((st = enqueue_dct_spectrum(N, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
+        const double hh = p->h;
+        const double scale = hh * hh * hh / ((2.0 * N) * (2.0 * N) * (2.0 * N));
+        e = dtype == FSP_F64 ? launch_store_S<double>((double *)Td.p, p->S, N, p->P, scale, s)
+                             : launch_store_S<float>((double *)Td.p, p->S, N, p->P, scale, s);
+        if (e != cudaSuccess) return fail(FSP_ECUDA);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FSP_ECUDA);
+    }
+    p->precompute_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    p->magic = kMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_plans.insert(p);
+    }
+    *out = p;
+    return FSP_OK;
+}
+
+fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stream) {
+    if (!plan_live(plan)) return FSP_EINVAL;
+    if (!rho || !phi || !aligned16(rho) || !aligned16(phi)) return FSP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    if (dev != plan->device) return FSP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = plan->dtype == FSP_F64 ? enqueue_solve<double>(plan, rho, phi, s)
+                                           : enqueue_solve<float>(plan, rho, phi, s);
+    return cuda_status(e);
+}
+
+fsp_status fsp_solve_host(fsp_plan *plan, const void *rho_host, void *phi_host, fsp_stream stream) {
+    if (!plan_live(plan)) return FSP_EINVAL;
+    if (!rho_host || !phi_host) return FSP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    if (dev != plan->device) return FSP_EINVAL;
+    const size_t bytes = (size_t)plan->N * plan->N * plan->N * plan->rsize;
+    if (!plan->stage_rho) {
+        DevBuf a, b;
+        fsp_status st;
+        if ((st = alloc_or_nomem(a, bytes)) != FSP_OK) return st;
+        if ((st = alloc_or_nomem(b, bytes)) != FSP_OK) return st;
+        plan->stage_rho = a.release();
+        plan->stage_phi = b.release();
+        plan->bytes += 2 * bytes;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    FSP_TRY_CUDA(cudaMemcpyAsync(plan->stage_rho, rho_host, bytes, cudaMemcpyHostToDevice, s));
+    fsp_status st = fsp_solve(plan, plan->stage_rho, plan->stage_phi, stream);
+    if (st != FSP_OK) return st;
+    FSP_TRY_CUDA(cudaMemcpyAsync(phi_host, plan->stage_phi, bytes, cudaMemcpyDeviceToHost, s));
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+fsp_status fsp_plan_sync(fsp_plan *plan, fsp_stream stream) {
+    if (!plan_live(plan)) return FSP_EINVAL;
+    return cuda_status(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fsp_status fsp_plan_destroy(fsp_plan *plan) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!plan || !g_plans.count(plan)) return FSP_EINVAL;
+        g_plans.erase(plan);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    plan_free(plan);
+    return cuda_status(e);
+}
+
+fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents) {
+    if (!plan_live(plan)) return FSP_EINVAL;
+    if (nevents == 0) {
+        plan->timing = false;
+        return FSP_OK;
+    }
+    if (nevents != 6 || !events) return FSP_EINVAL;
+    for (int i = 0; i < 6; ++i)
+        if (!events[i]) return FSP_EINVAL;
+    for (int i = 0; i < 6; ++i) plan->ev[i] = reinterpret_cast<cudaEvent_t>(events[i]);
+    plan->timing = true;
+    return FSP_OK;
+}
+
+size_t fsp_plan_bytes(const fsp_plan *plan) { return plan_live(plan) ? plan->bytes : 0; }
+
+double fsp_plan_precompute_ms(const fsp_plan *plan) { return plan_live(plan) ? plan->precompute_ms : -1.0; }
+
+fsp_status fsp_plan_spectrum(const fsp_plan *plan, double *s_host) {
+    if (!plan_live(plan) || !s_host) return FSP_EINVAL;
+    const size_t k1 = plan->N + 1, tot = k1 * k1 * k1;
+    DevBuf d;
+    fsp_status st = alloc_or_nomem(d, sizeof(double) * tot);
+    if (st != FSP_OK) return st;
+    cudaError_t e = plan->dtype == FSP_F64 ? launch_load_S<double>(plan->S, (double *)d.p, plan->N, plan->P, 0)
+                                           : launch_load_S<float>(plan->S, (double *)d.p, plan->N, plan->P, 0);
+    if (e != cudaSuccess) return FSP_ECUDA;
+    return cuda_status(cudaMemcpy(s_host, d.p, sizeof(double) * tot, cudaMemcpyDeviceToHost));
+}
+
+fsp_status fsp_kernel_T(int N, double L, fsp_algo algo, double *t_dev, fsp_stream stream) {
+    fsp_status st = validate_size(N, L, algo);
+    if (st != FSP_OK) return st;
+    if (!t_dev || !aligned16(t_dev)) return FSP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Temps tmp;
+    st = enqueue_kernel_T(N, L, algo, t_dev, s, tmp);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (st != FSP_OK) return st;
+    return cuda_status(e);
+}
+
+fsp_status fsp_fft_c2c(int n, int count, fsp_dtype dtype, int sign, const void *in, void *out, fsp_stream stream) {
+    if (n < 1 || n > 4096 || count < 0 || (sign != -1 && sign != 1)) return FSP_EINVAL;
+    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED) return FSP_EINVAL;
+    if (!is_235_smooth(n)) return FSP_EUNSUPPORTED;
+    if (count == 0) return FSP_OK;
+    if (!in || !out || !aligned16(in) || !aligned16(out)) return FSP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    const size_t csize = dtype == FSP_F64 ? 16 : 8;
+    TileCfg c;
+    if (!make_cfg(n, n, csize, dtype == FSP_F64 ? 3 : 4, c)) return FSP_EUNSUPPORTED;
+    // roots tables are cached per (device, dtype, n) for the life of the process
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, void *> cache;
+    void *tw = nullptr;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto key = std::make_tuple(dev, (int)dtype, n);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            tw = it->second;
+        } else {
+            DevBuf b;
+            fsp_status st = alloc_or_nomem(b, csize * n);
+            if (st != FSP_OK) return st;
+            cudaError_t e = dtype == FSP_F64 ? launch_roots<double>(b.p, n, s) : launch_roots<float>(b.p, n, s);
+            if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return FSP_ECUDA;
+            tw = b.release();
+            cache[key] = tw;
+        }
+    }
+    LinesArgs a{};
+    a.in = in, a.out = out, a.tw = tw, a.st = c.st, a.tpl = c.tpl, a.lgL = c.lgL;
+    a.in_pos = a.out_pos = 1, a.in_line = a.out_line = n, a.in_batch = a.out_batch = 0;
+    a.n_in = a.n_out = n, a.nlines = count, a.nbatch = 1;
+    cudaError_t e;
+    if (dtype == FSP_F64)
+        e = sign < 0 ? launch_lines<double, IN_CPLX, OUT_CPLX, M_FWD>(a, s)
+                     : launch_lines<double, IN_CPLX, OUT_CPLX, M_INV>(a, s);
+    else
+        e = sign < 0 ? launch_lines<float, IN_CPLX, OUT_CPLX, M_FWD>(a, s)
+                     : launch_lines<float, IN_CPLX, OUT_CPLX, M_INV>(a, s);
+    return cuda_status(e);
+}
+
+}  // extern "C"

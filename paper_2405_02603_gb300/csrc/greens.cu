@@ -1,0 +1,146 @@
+// greens.cu -- plan-time sampling kernels of the Green's functions (always
+// FP64): the Hockney-Eastwood kernel (Sec. 2.2 step 3), the Vico-Greengard
+// truncated spectral kernel sampled on the (4N)^3 frequency grid (Sec. 2.3,
+// Eq. green_vico) and on its (2N+1)^3 non-negative octant (Sec. 2.4), plus
+// scaling and the rounding of the spectrum to the solve's type.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "greens.h"
+
+namespace fsp {
+
+// 1/(4 pi)
+__device__ __forceinline__ double inv4pi() { return 0.079577471545947667884441881686257; }
+
+// Eq. green_vico: G_L(k) = 2 (sin(L_t |k| / 2) / |k|)^2, evaluated as
+// 2 (L_t/2)^2 sinc^2(u), u = L_t |k| / 2; for |u| < 1e-3 the sinc uses its
+// Taylor series 1 - u^2/6 + u^4/120 (truncation below u^6/5040), so the k -> 0
+// limit L_t^2 / 2 is reached without cancellation.
+__device__ __forceinline__ double green_vico_hat(double kabs, double Lt) {
+    const double u = 0.5 * Lt * kabs;
+    double s;
+    if (fabs(u) < 1e-3) {
+        const double u2 = u * u;
+        s = 1.0 - u2 / 6.0 + u2 * u2 / 120.0;
+    } else {
+        s = sin(u) / u;
+    }
+    const double hl = 0.5 * Lt;
+    return 2.0 * hl * hl * s * s;
+}
+
+// T[m] = 1/(4 pi h |m|), T[0] = 1/(4 pi); m in [0,N]^3, x fastest.
+__global__ void k_he_T(double *T, int N, double h) {
+    const int k1 = N + 1;
+    const long long tot = (long long)k1 * k1 * k1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % k1), y = (int)((i / k1) % k1), z = (int)(i / ((long long)k1 * k1));
+        const double r = sqrt((double)x * x + (double)y * y + (double)z * z);
+        T[i] = (x | y | z) ? inv4pi() / (h * r) : inv4pi();
+    }
+}
+
+// g[j] = G_L(dk |j|) for j in [0,M]^3 (M = 2N), dk = 2 pi / (4 N h).
+__global__ void k_vg_sample_octant(double *g, int M, double dk, double Lt) {
+    const int n = M + 1;
+    const long long tot = (long long)n * n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+        g[i] = green_vico_hat(dk * sqrt((double)x * x + (double)y * y + (double)z * z), Lt);
+    }
+}
+
+// g[s] = G_L(dk |j|) on the (4N)^3 grid, storage index s holding frequency
+// j = s for s < 2N and j = s - 4N otherwise (the Nyquist plane j = -2N
+// included).  Complex, imaginary part zero.
+__global__ void k_vg_sample_full(double2 *g, int n4, double dk, double Lt) {
+    const long long tot = (long long)n4 * n4 * n4;
+    const int half = n4 / 2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(i % n4), y = (int)((i / n4) % n4), z = (int)(i / ((long long)n4 * n4));
+        x = x < half ? x : x - n4;
+        y = y < half ? y : y - n4;
+        z = z < half ? z : z - n4;
+        g[i] = double2{green_vico_hat(dk * sqrt((double)x * x + (double)y * y + (double)z * z), Lt), 0.0};
+    }
+}
+
+__global__ void k_scale(double *a, long long n, double s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] *= s;
+}
+
+// S[qz][qy][qx] (row pitch P) = scale * Sd[qz][qy][qx] rounded to T.
+template <typename T> __global__ void k_store_S(const double *Sd, T *S, int N, int P, double scale) {
+    const int k1 = N + 1;
+    const long long tot = (long long)k1 * k1 * k1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % k1);
+        const long long row = i / k1;  // qz*(N+1) + qy
+        S[row * P + x] = (T)(scale * Sd[i]);
+    }
+}
+
+// S (pitch P, type T) -> dense (N+1)^3 doubles
+template <typename T> __global__ void k_load_S(const T *S, double *Sd, int N, int P) {
+    const int k1 = N + 1;
+    const long long tot = (long long)k1 * k1 * k1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % k1);
+        Sd[i] = (double)S[(i / k1) * P + x];
+    }
+}
+
+static unsigned grid_for(long long tot) {
+    long long b = (tot + 255) / 256;
+    if (b > 152LL * 64) b = 152LL * 64;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+cudaError_t launch_he_T(double *T, int N, double h, cudaStream_t s) {
+    const long long tot = (long long)(N + 1) * (N + 1) * (N + 1);
+    k_he_T<<<grid_for(tot), 256, 0, s>>>(T, N, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vg_sample_octant(double *g, int N, double h, double Lt, cudaStream_t s) {
+    const int M = 2 * N;
+    const long long tot = (long long)(M + 1) * (M + 1) * (M + 1);
+    const double dk = 6.283185307179586476925286766559 / (4.0 * N * h);
+    k_vg_sample_octant<<<grid_for(tot), 256, 0, s>>>(g, M, dk, Lt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vg_sample_full(void *g, int N, double h, double Lt, cudaStream_t s) {
+    const int n4 = 4 * N;
+    const long long tot = (long long)n4 * n4 * n4;
+    const double dk = 6.283185307179586476925286766559 / (4.0 * N * h);
+    k_vg_sample_full<<<grid_for(tot), 256, 0, s>>>(reinterpret_cast<double2 *>(g), n4, dk, Lt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double *a, long long n, double sc, cudaStream_t s) {
+    k_scale<<<grid_for(n), 256, 0, s>>>(a, n, sc);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_store_S(const double *Sd, void *S, int N, int P, double scale, cudaStream_t s) {
+    const long long tot = (long long)(N + 1) * (N + 1) * (N + 1);
+    k_store_S<T><<<grid_for(tot), 256, 0, s>>>(Sd, reinterpret_cast<T *>(S), N, P, scale);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_load_S(const void *S, double *Sd, int N, int P, cudaStream_t s) {
+    const long long tot = (long long)(N + 1) * (N + 1) * (N + 1);
+    k_load_S<T><<<grid_for(tot), 256, 0, s>>>(reinterpret_cast<const T *>(S), Sd, N, P);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_store_S<float>(const double *, void *, int, int, double, cudaStream_t);
+template cudaError_t launch_store_S<double>(const double *, void *, int, int, double, cudaStream_t);
+template cudaError_t launch_load_S<float>(const void *, double *, int, int, cudaStream_t);
+template cudaError_t launch_load_S<double>(const void *, double *, int, int, cudaStream_t);
+
+}  // namespace fsp

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every entry point of
+include/fsp.h; host-side validation rejects bad arguments before any device
+work (no GPU needed for these calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fsp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fsp_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_2405_02603_gb300 as fsp
+    return fsp.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = declared_symbols()
+    assert len(syms) >= 10
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_status_strings(L):
+    for code in range(7):
+        assert L.fsp_status_str(code).startswith(b"FSP_")
+    assert L.fsp_status_str(99).startswith(b"FSP_?")
+
+
+def test_plan_create_validation_needs_no_device(L):
+    p = ctypes.c_void_p()
+    bad = [(1, 1.0, 1.0, 0, 0), (0, 1.0, 0.1, 0, 0), (8, -1.0, -0.125, 0, 0), (8, 1.0, 0.2, 0, 0),
+           (8, 1.0, 0.125, 7, 0), (8, 1.0, 0.125, 0, 5), (8, float("inf"), 0.1, 0, 0)]
+    for N, Lb, h, algo, dt in bad:
+        assert L.fsp_plan_create(ctypes.byref(p), N, Lb, h, algo, dt, None) == 1, (N, Lb, h, algo, dt)
+        assert not p.value
+    # 2N not 2/3/5-smooth, and N above the supported maximum
+    assert L.fsp_plan_create(ctypes.byref(p), 7, 1.0, 1.0 / 7, 0, 0, None) == 2
+    assert L.fsp_plan_create(ctypes.byref(p), 2048, 1.0, 1.0 / 2048, 0, 0, None) == 2
+    assert L.fsp_plan_create(None, 8, 1.0, 0.125, 0, 0, None) == 1
+
+
+def test_unknown_plan_is_rejected(L):
+    fake = ctypes.c_void_p(0x1000)
+    assert L.fsp_solve(fake, fake, fake, None) == 1
+    assert L.fsp_solve(None, fake, fake, None) == 1
+    assert L.fsp_plan_destroy(fake) == 1
+    assert L.fsp_plan_destroy(None) == 1
+    assert L.fsp_plan_bytes(fake) == 0
+    assert L.fsp_plan_precompute_ms(fake) < 0
+    assert L.fsp_plan_spectrum(fake, fake) == 1
+    assert L.fsp_plan_sync(fake, None) == 1
+
+
+def test_fft_and_kernel_validation(L):
+    assert L.fsp_fft_c2c(7, 1, 0, -1, None, None, None) == 2
+    assert L.fsp_fft_c2c(8, 1, 0, 0, None, None, None) == 1
+    assert L.fsp_fft_c2c(8, 0, 0, -1, None, None, None) == 0  # nothing to do
+    assert L.fsp_fft_c2c(8, 1, 3, -1, None, None, None) == 1
+    assert L.fsp_kernel_T(1, 1.0, 0, None, None) == 1
+    assert L.fsp_kernel_T(8, 1.0, 0, None, None) == 1
+    assert L.fsp_kernel_T(11, 1.0, 0, None, None) == 2
+
+
+def test_product_does_not_reference_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2405_02603_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "fsp_oracle" not in text, f

@@ -1,0 +1,69 @@
+"""Parity at the benchmark's sizes, in the launch configuration bench.py times.
+
+N = 256: the whole field against the oracle's full (2N)^3 FFT solve; the
+source is the seeded 8-Gaussian mixture rounded to float32 once, so the same
+array is exact input for both precisions (one oracle solve serves both).  The
+oracle's Vico-Greengard kernel comes from its direct DCT-I route, which its
+own pins tie to the (4N)^3 route to 1e-16.
+
+N = 512: Hockney-Eastwood at sampled points against the oracle's direct O(N^3)
+sum per point; Vico-Greengard against the analytic potential of the centred
+Gaussian (spectrally accurate, so the discretisation error is far below the
+FP64 tolerance at this size)."""
+import numpy as np
+import pytest
+
+import fsp_inputs as I
+from conftest import e_max, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6}
+
+
+@pytest.fixture(scope="module")
+def ref256(orc):
+    N, L = 256, 1.0
+    rho = I.gaussian_mixture(N).astype(np.float32).astype(np.float64)
+    T = orc.kernel_T("vg_dct", N, L)
+    return N, L, rho, orc.solve_fft(T, rho, L / N)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("algo", ["vg", "vg_dct"])
+def test_n256_full_field(fsp, ref256, algo, dtype):
+    N, L, rho, ref = ref256
+    p = fsp.Plan(N, L, algo, dtype)
+    phi = p.solve(to_dev(rho, dtype)).cpu().numpy()
+    err = e_max(phi, ref)
+    print("N=256 %s %s E_max vs oracle = %.3e" % (algo, dtype, err))
+    assert err <= TOL[dtype]
+    p.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_n512_he_sampled_direct_sum(fsp, orc, dtype):
+    N, L = 512, 1.0
+    h = L / N
+    rho = I.gaussian_mixture(N, seed=2405).astype(np.float32).astype(np.float64)
+    p = fsp.Plan(N, L, "he", dtype)
+    phi = p.solve(to_dev(rho, dtype)).cpu().numpy().ravel()
+    rng = np.random.default_rng(512)
+    pts = np.concatenate([rng.integers(0, N ** 3, 20), [0, N ** 3 - 1, (N // 2) * (N * N + N + 1)]])
+    T = orc.kernel_T("he", N, L)
+    ref = orc.solve_direct(T, rho, h, pts)
+    err = float(np.max(np.abs(phi[pts] - ref)) / np.max(np.abs(ref)))
+    print("N=512 he %s sampled E_max vs direct sum = %.3e" % (dtype, err))
+    assert err <= TOL[dtype]
+    p.close()
+
+
+def test_n512_vg_against_analytic(fsp):
+    from oracle import analytic as A
+    N = 512
+    p = fsp.Plan(N, 1.0, "vg_dct", "f64")
+    phi = p.solve(to_dev(I.gaussian(N))).cpu().numpy()
+    err = A.e_max(phi, A.gaussian_potential(N))
+    print("N=512 vg_dct f64 E_max vs analytic = %.3e" % err)
+    assert err <= 1e-12
+    p.close()

@@ -166,6 +166,35 @@ fsp_status fsp_kernel_T(int N, double L, fsp_algo algo, double *t_dev, fsp_strea
  */
 fsp_status fsp_fft_c2c(int n, int count, fsp_dtype dtype, int sign, const void *in, void *out, fsp_stream stream);
 
+/*
+ * fsp_solve_noalloc -- an FP64 solve that allocates no device memory.  The
+ * paper has no counterpart: it is an interface for callers that cannot call
+ * cudaMalloc (code running while a CUDA graph is captured in global mode,
+ * where the runtime rejects allocations; real-time loops that forbid allocator
+ * calls; applications whose device memory is entirely held by their own
+ * allocator).  The caller passes everything that has a size: the spectrum,
+ * the source and the result.
+ *
+ * N    2 <= N <= 32 and 2N 2/3/5-smooth; larger or unsupported sizes return
+ *      FSP_EUNSUPPORTED (N < 2: FSP_EINVAL) before any device work.
+ * S    DEVICE array of (N+1)^3 doubles, index (qz*(N+1)+qy)*(N+1)+qx: the
+ *      multiplier of the method, h^3 DFT_{2N}{G_2}[q] / (2N)^3, e.g. what
+ *      fsp_plan_spectrum returns for an FSP_F64 plan, copied to the device.
+ * rho, phi  DEVICE arrays of N^3 doubles, 16-byte aligned (as fsp_solve).
+ *
+ * Scratch: the two transform buffers and the roots tables live in one
+ * file-scope device array of 2.36 MB (N = 32 at row pitch 48), which every
+ * GPU that loads the library holds until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress) and
+ * keeps it; make that first call before any stream capture.  All calls on a
+ * device share the one array and leave their intermediate values in it; no
+ * part of it needs to start at zero (each call writes every element before
+ * reading it).  Calls whose device work overlaps in time (different streams,
+ * or host threads racing on one device) corrupt each other's results:
+ * serialise them, e.g. on one stream.  Asynchronous on `stream`.
+ */
+fsp_status fsp_solve_noalloc(int N, const double *S, const double *rho, double *phi, fsp_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,8 +64,9 @@ def lib(build_if_missing=True):
     L.fsp_kernel_T.argtypes = [i, d, i, vp, vp]
     L.fsp_fft_c2c.argtypes = [i, i, i, i, vp, vp, vp]
     L.fsp_plan_set_timing.argtypes = [vp, ctypes.POINTER(vp), i]
+    L.fsp_solve_noalloc.argtypes = [i, vp, vp, vp, vp]
     for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
-                 "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c"):
+                 "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -187,6 +188,25 @@ def kernel_T(N, L=1.0, algo="vg_dct", stream=None):
     return t
 
 
+def solve_noalloc(S, rho, phi, stream=None):
+    """FP64 solve for N <= 32 with no device allocation (fsp_solve_noalloc).
+
+    S: CUDA float64 tensor of (N+1)^3 spectrum values (e.g. Plan.spectrum()
+    copied to the device); rho, phi: CUDA float64 tensors of N^3 values.
+    For callers that cannot allocate device memory; calls share one static
+    scratch array, so calls that overlap on the GPU must not be issued."""
+    import torch
+    N = round(rho.numel() ** (1.0 / 3.0))
+    for t in (S, rho, phi):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.float64):
+            raise FspError(FSP_EINVAL, "solve_noalloc wants contiguous CUDA float64 tensors")
+    if rho.numel() != N ** 3 or phi.numel() != N ** 3 or S.numel() != (N + 1) ** 3:
+        raise FspError(FSP_EINVAL, "solve_noalloc: sizes must be N^3, N^3 and (N+1)^3")
+    check(lib().fsp_solve_noalloc(int(N), ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+                                  ctypes.c_void_p(phi.data_ptr()), _stream_handle(stream)), "fsp_solve_noalloc")
+    return phi
+
+
 def fft_c2c(x, sign=-1, stream=None):
     """Batched 1D FFTs along the last axis of a complex CUDA tensor (library kernels)."""
     import torch
@@ -202,4 +222,4 @@ def fft_c2c(x, sign=-1, stream=None):
     return out
 
 
-__all__ = ["Plan", "FspError", "kernel_T", "fft_c2c", "lib", "check", "library_path", "ALGOS", "DTYPES"]
+__all__ = ["Plan", "FspError", "kernel_T", "fft_c2c", "solve_noalloc", "lib", "check", "library_path", "ALGOS", "DTYPES"]

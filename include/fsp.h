@@ -131,6 +131,13 @@ fsp_status fsp_plan_destroy(fsp_plan *plan);
  */
 fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents);
 
+/* 1 when this plan's solves run the specialised power-of-two kernels (N = 32,
+ * 64, 128, 256, 512; compile-time radix schedules, register-resident), 0 when
+ * they run the generic mixed-radix engine, -1 for an invalid plan.  Setting
+ * the environment variable FSP_GENERIC_ONLY=1 before fsp_plan_create forces
+ * the generic engine (used to test both paths on the same sizes). */
+int fsp_plan_uses_fast_path(const fsp_plan *plan);
+
 /* Device bytes the plan holds (spectrum + workspace + tables), 0 if invalid. */
 size_t fsp_plan_bytes(const fsp_plan *plan);
 

@@ -65,6 +65,8 @@ def lib(build_if_missing=True):
     L.fsp_fft_c2c.argtypes = [i, i, i, i, vp, vp, vp]
     L.fsp_plan_set_timing.argtypes = [vp, ctypes.POINTER(vp), i]
     L.fsp_solve_noalloc.argtypes = [i, vp, vp, vp, vp]
+    L.fsp_plan_uses_fast_path.argtypes = [vp]
+    L.fsp_plan_uses_fast_path.restype = i
     for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
                  "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc"):
         getattr(L, name).restype = i
@@ -115,6 +117,11 @@ class Plan:
     @property
     def bytes(self):
         return int(lib().fsp_plan_bytes(self._p))
+
+    @property
+    def fast_path(self):
+        """True when the specialised power-of-two kernels serve this plan."""
+        return lib().fsp_plan_uses_fast_path(self._p) == 1
 
     @property
     def precompute_ms(self):

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -12,6 +13,7 @@
 #include <unordered_set>
 
 #include "../../include/fsp.h"
+#include "fast.h"
 #include "greens.h"
 #include "kernels.cuh"
 
@@ -259,6 +261,7 @@ struct fsp_plan {
     void *S = nullptr, *W1 = nullptr, *W2 = nullptr, *tw_n = nullptr, *tw_2n = nullptr;
     void *stage_rho = nullptr, *stage_phi = nullptr;
     TileCfg row, col;
+    bool fast = false;  // specialised power-of-two kernels (fast.cuh) serve this N
     cudaEvent_t ev[6] = {};
     bool timing = false;
     size_t bytes = 0;
@@ -279,7 +282,37 @@ void plan_free(fsp_plan *p) {
     delete p;
 }
 
-template <typename T> cudaError_t enqueue_solve(const fsp_plan *p, const void *rho, void *phi, cudaStream_t s) {
+template <typename T> cudaError_t enqueue_solve_fast(const fsp_plan *p, const void *rho, void *phi, cudaStream_t s) {
+    const int N = p->N;
+    const long long P = p->P;
+    cudaError_t e;
+    auto mark = [&](int i) { return p->timing ? cudaEventRecord(p->ev[i], s) : cudaSuccess; };
+    fast::RowArgs r{};
+    r.x = rho, r.c = p->W1, r.x_row = N, r.c_row = P, r.nrows = N * N, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    fast::ColArgs a{};
+    a.tw = p->tw_2n, a.nlines = N + 1;
+    if ((e = mark(0)) != cudaSuccess) return e;
+    if ((e = fast::p1<T>(N, r, s)) != cudaSuccess) return e;  // P1: pad + x-R2C
+    if ((e = mark(1)) != cudaSuccess) return e;
+    a.in = p->W1, a.out = p->W2;  // P2: y-FFT, W1[z][y][kx] -> W2[z][ky][kx]
+    a.in_pos = P, a.in_batch = (long long)N * P, a.out_pos = P, a.out_batch = 2LL * N * P;
+    if ((e = fast::p2<T>(N, a, N, s)) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
+    a.in = a.out = p->W2;  // P3: z-FFT * S * z-IFFT, in place, batch ky
+    a.in_pos = a.out_pos = 2LL * N * P, a.in_batch = a.out_batch = P;
+    a.S = p->S, a.s_pos = (long long)(N + 1) * P, a.s_batch = P, a.half = N;
+    if ((e = fast::p3<T>(N, a, 2 * N, s)) != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
+    a.in = p->W2, a.out = p->W1;  // P4: y-IFFT, W2 -> W1 (y < N)
+    a.in_pos = P, a.in_batch = 2LL * N * P, a.out_pos = P, a.out_batch = (long long)N * P;
+    if ((e = fast::p4<T>(N, a, N, s)) != cudaSuccess) return e;
+    if ((e = mark(4)) != cudaSuccess) return e;
+    r.x = phi;  // P5: x-C2R, W1 rows -> phi
+    if ((e = fast::p5<T>(N, r, s)) != cudaSuccess) return e;
+    return mark(5);
+}
+
+template <typename T> cudaError_t enqueue_solve_generic(const fsp_plan *p, const void *rho, void *phi, cudaStream_t s) {
     const int N = p->N;
     const long long P = p->P;
     cudaError_t e;
@@ -363,6 +396,12 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
         delete p;
         return FSP_ECUDA;
     }
+    // specialised kernels for power-of-two N unless FSP_GENERIC_ONLY=1 (A/B and tests)
+    {
+        const char *g = std::getenv("FSP_GENERIC_ONLY");
+        const bool generic_only = g && g[0] == '1';
+        p->fast = !generic_only && (dtype == FSP_F64 ? fast::has<double>(N) : fast::has<float>(N));
+    }
     auto fail = [&](fsp_status e) {
         cudaStreamSynchronize(s);
         plan_free(p);
@@ -420,8 +459,13 @@ fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stre
     if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
     if (dev != plan->device) return FSP_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = plan->dtype == FSP_F64 ? enqueue_solve<double>(plan, rho, phi, s)
-                                           : enqueue_solve<float>(plan, rho, phi, s);
+    cudaError_t e;
+    if (plan->fast)
+        e = plan->dtype == FSP_F64 ? enqueue_solve_fast<double>(plan, rho, phi, s)
+                                   : enqueue_solve_fast<float>(plan, rho, phi, s);
+    else
+        e = plan->dtype == FSP_F64 ? enqueue_solve_generic<double>(plan, rho, phi, s)
+                                   : enqueue_solve_generic<float>(plan, rho, phi, s);
     return cuda_status(e);
 }
 
@@ -478,6 +522,8 @@ fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents)
     plan->timing = true;
     return FSP_OK;
 }
+
+int fsp_plan_uses_fast_path(const fsp_plan *plan) { return plan_live(plan) ? (plan->fast ? 1 : 0) : -1; }
 
 size_t fsp_plan_bytes(const fsp_plan *plan) { return plan_live(plan) ? plan->bytes : 0; }
 

@@ -1,0 +1,536 @@
+// fast.cuh -- compile-time specialised, register-resident line transforms for
+// power-of-two lengths (the solve passes P1..P5 for N = 32..512).
+//
+// Compared with the generic shared-memory engine (fft_engine.cuh):
+//  * the radix schedule, strides and tile shape are template constants, so all
+//    index arithmetic folds into immediate offsets;
+//  * every thread keeps V values in registers; only the exchanges between
+//    stages go through shared memory;
+//  * the first stage of a zero-padded transform reads straight from global
+//    memory and skips the zero half (its butterflies have half-zero inputs),
+//    and the last stage of a cropped transform computes and stores only the
+//    kept half (Sec. 2.2 steps 2 and 5, pruned);
+//  * in P3 the multiply by S happens in registers and the inverse transform
+//    runs the forward radix schedule in reverse, so its first stage works on
+//    the very registers the forward's last stage produced (no exchange).
+//
+// Stage s (radix R, Ns = product of the earlier radices) on butterflies
+// b = t + k*TPL (k < V/R) of thread t: inputs at positions b + r n/R,
+// twiddles w_n^(r (b mod Ns) n/(Ns R)), outputs at (b - b mod Ns) R +
+// b mod Ns + r Ns -- the self-sorting Stockham form of the generic engine.
+#pragma once
+#include <utility>
+
+#include "fast.h"
+#include "kernels.cuh"
+
+namespace fsp {
+namespace fast {
+
+// ------------------------------------------------------------ constants --
+// cos(2 pi m / 32), m in [0, 8]
+__host__ __device__ constexpr double c32_base(int m) {
+    return m == 0   ? 1.0
+           : m == 1 ? 0.98078528040323044912618
+           : m == 2 ? 0.92387953251128675612818
+           : m == 3 ? 0.83146961230254523707879
+           : m == 4 ? 0.70710678118654752440084
+           : m == 5 ? 0.55557023301960222474283
+           : m == 6 ? 0.38268343236508977172846
+           : m == 7 ? 0.19509032201612826784828
+                    : 0.0;
+}
+__host__ __device__ constexpr double cos32(int m) {
+    m &= 31;
+    return m <= 8 ? c32_base(m) : m <= 16 ? -c32_base(16 - m) : m <= 24 ? -c32_base(m - 16) : c32_base(32 - m);
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+template <int I, int E> struct StaticFor {
+    template <class F> static __device__ __forceinline__ void run(F &&f) {
+        if constexpr (I < E) {
+            f(std::integral_constant<int, I>{});
+            StaticFor<I + 1, E>::run(f);
+        }
+    }
+};
+
+// ------------------------------------------------------- register DFTs --
+// v'[q] = sum_r v[r] exp(D 2 pi i r q / R).  HZ: inputs r >= R/2 are zero
+// (not read).  HO: only outputs q < R/2 are produced.
+template <typename T, int D> struct RD {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ C rot(C a) { return D < 0 ? cmulmi(a) : cmuli(a); }  // exp(D i pi/2)
+
+    // multiply by exp(D 2 pi i M / 32)
+    template <int M> static __device__ __forceinline__ C w32(C a) {
+        constexpr int m = ((M % 32) + 32) % 32;
+        if constexpr (m == 0) {
+            return a;
+        } else if constexpr (m == 8) {
+            return rot(a);
+        } else if constexpr (m == 16) {
+            return C{-a.x, -a.y};
+        } else if constexpr (m == 24) {
+            return D < 0 ? cmuli(a) : cmulmi(a);
+        } else {
+            constexpr T c = T(cos32(m)), s = T(D * sin32(m));
+            return C{c * a.x - s * a.y, s * a.x + c * a.y};
+        }
+    }
+
+    template <bool HZ, bool HO> static __device__ __forceinline__ void d2(C *v) {
+        if constexpr (HZ) {
+            v[1] = v[0];
+        } else {
+            const C a = v[0], b = v[1];
+            v[0] = cadd(a, b);
+            if constexpr (!HO) v[1] = csub(a, b);
+        }
+    }
+    template <bool HZ, bool HO> static __device__ __forceinline__ void d4(C *v) {
+        C t0, t1, t2, t3;
+        if constexpr (HZ) {
+            t0 = v[0], t1 = v[0], t2 = v[1], t3 = rot(v[1]);
+        } else {
+            t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+            t2 = cadd(v[1], v[3]), t3 = rot(csub(v[1], v[3]));
+        }
+        v[0] = cadd(t0, t2);
+        v[1] = cadd(t1, t3);
+        if constexpr (!HO) {
+            v[2] = csub(t0, t2);
+            v[3] = csub(t1, t3);
+        }
+    }
+    template <bool HZ, bool HO> static __device__ __forceinline__ void d8(C *v) {
+        C e[4], o[4];
+        e[0] = v[0], e[1] = v[2], o[0] = v[1], o[1] = v[3];
+        if constexpr (!HZ) e[2] = v[4], e[3] = v[6], o[2] = v[5], o[3] = v[7];
+        d4<HZ, false>(e);
+        d4<HZ, false>(o);
+        o[1] = w32<4>(o[1]);
+        o[2] = w32<8>(o[2]);
+        o[3] = w32<12>(o[3]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = cadd(e[q], o[q]);
+        if constexpr (!HO) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q + 4] = csub(e[q], o[q]);
+        }
+    }
+    // R = 4 B (B = 4 or 8): x[B n1 + n2] -> DFT_4 over n1 per n2, twiddle
+    // w_R^(n2 k1), DFT_B over n2 per k1 -> X[k1 + 4 k2].
+    template <int R, bool HZ, bool HO> static __device__ __forceinline__ void dct4(C *v) {
+        constexpr int B = R / 4;
+        C y[R];
+        StaticFor<0, B>::run([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            C g[4];
+            g[0] = v[n2], g[1] = v[B + n2];
+            if constexpr (!HZ) g[2] = v[2 * B + n2], g[3] = v[3 * B + n2];
+            d4<HZ, false>(g);
+            y[n2 * 4 + 0] = g[0];
+            y[n2 * 4 + 1] = w32<n2 * 1 * (32 / R)>(g[1]);
+            y[n2 * 4 + 2] = w32<n2 * 2 * (32 / R)>(g[2]);
+            y[n2 * 4 + 3] = w32<n2 * 3 * (32 / R)>(g[3]);
+        });
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C h[B];
+#pragma unroll
+            for (int n2 = 0; n2 < B; ++n2) h[n2] = y[n2 * 4 + k1];
+            if constexpr (B == 4)
+                d4<false, HO>(h);
+            else
+                d8<false, HO>(h);
+#pragma unroll
+            for (int k2 = 0; k2 < (HO ? B / 2 : B); ++k2) v[k1 + 4 * k2] = h[k2];
+        }
+    }
+    template <int R, bool HZ, bool HO> static __device__ __forceinline__ void dft(C *v) {
+        if constexpr (R == 2)
+            d2<HZ, HO>(v);
+        else if constexpr (R == 4)
+            d4<HZ, HO>(v);
+        else if constexpr (R == 8)
+            d8<HZ, HO>(v);
+        else
+            dct4<R, HZ, HO>(v);
+    }
+};
+
+// ---------------------------------------------------------------- stages --
+// n: transform length; V: values per thread; L: lines per CTA (pitch L+1).
+template <typename T, int D, int n, int V, int L> struct Stg {
+    using C = cx_t<T>;
+    static constexpr int TPL = n / V;
+    static constexpr int LD = L + 1;
+
+    // exp(D 2 pi i e / n) from the forward roots table
+    static __device__ __forceinline__ C twid(const C *__restrict__ tw, int e) {
+        C w = __ldg(tw + e);
+        if (D > 0) w.y = -w.y;
+        return w;
+    }
+
+    template <int R, int Ns, bool HZ, bool HO>
+    static __device__ __forceinline__ void compute(C *v, int t, const C *__restrict__ tw) {
+        static_assert(V % R == 0, "radix must divide the values per thread");
+        StaticFor<0, V / R>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            if constexpr (Ns > 1) {
+                const unsigned b = (unsigned)(t + k * TPL);
+                const unsigned j = b % (unsigned)Ns;
+                constexpr int tws = n / (Ns * R);
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], twid(tw, (int)(r * j) * tws));
+            }
+            RD<T, D>::template dft<R, HZ, HO>(v + k * R);
+        });
+    }
+
+    template <int R> static __device__ __forceinline__ void load_in(C *v, const C *buf, int t, int l) {
+#pragma unroll
+        for (int k = 0; k < V / R; ++k)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k * R + r] = buf[(t + k * TPL + r * (n / R)) * LD + l];
+    }
+
+    template <int R, int Ns> static __device__ __forceinline__ void store_out(C *buf, const C *v, int t, int l) {
+#pragma unroll
+        for (int k = 0; k < V / R; ++k) {
+            const unsigned b = (unsigned)(t + k * TPL);
+            const unsigned j = b % (unsigned)Ns;
+            const int base = (int)((b - j) * R + j);
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[(base + r * Ns) * LD + l] = v[k * R + r];
+        }
+    }
+};
+
+// Run stages 1.. of schedule (R1, R2, R3) after stage 0 has been computed in
+// registers: exchange through shared memory, compute; leaves the last
+// stage's outputs in registers.  `first_sync` is needed when shared memory
+// was read just before (the caller's previous stage loaded from it).
+template <typename T, int D, int n, int V, int L, int R1, int R2, int R3, bool HO_LAST>
+__device__ __forceinline__ void run_rest(cx_t<T> *v, cx_t<T> *buf, int t, int l, const cx_t<T> *tw, bool first_sync) {
+    using S = Stg<T, D, n, V, L>;
+    if (first_sync) __syncthreads();
+    S::template store_out<R1, 1>(buf, v, t, l);
+    __syncthreads();
+    S::template load_in<R2>(v, buf, t, l);
+    if constexpr (R3 == 1) {
+        S::template compute<R2, R1, false, HO_LAST>(v, t, tw);
+    } else {
+        S::template compute<R2, R1, false, false>(v, t, tw);
+        __syncthreads();
+        S::template store_out<R2, R1>(buf, v, t, l);
+        __syncthreads();
+        S::template load_in<R3>(v, buf, t, l);
+        S::template compute<R3, R1 * R2, false, HO_LAST>(v, t, tw);
+    }
+}
+
+// Positions of the last stage's outputs: register k*R + r holds position
+// t + k*TPL + r*(n/R) (the last stage's butterflies have b < Ns).
+template <int R1, int R2, int R3> struct LastR {
+    static constexpr int value = R3 > 1 ? R3 : R2;
+};
+
+// ---------------------------------------------------- column pass kernel --
+// Lines are columns (consecutive lines contiguous in memory): P2 (COL_FWD,
+// half-zero input, all n outputs), P4 (COL_INV, all inputs, first n/2
+// outputs), P3 (COL_FMI: forward with half-zero input, times S, inverse, first
+// n/2 outputs).  The last tile may be partial (nlines not a multiple of L).
+template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE>
+__global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
+    using C = cx_t<T>;
+    constexpr int TPL = n / V;
+    constexpr int RL = LastR<R1, R2, R3>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int l = threadIdx.x % L, t = threadIdx.x / L;
+    const int line = blockIdx.x * L + l;
+    const bool ok = line < a.nlines;
+    const long long bt = blockIdx.y;
+    const C *tw = reinterpret_cast<const C *>(a.tw);
+    const C *in = reinterpret_cast<const C *>(a.in) + bt * a.in_batch + line;
+    C *out = reinterpret_cast<C *>(a.out) + bt * a.out_batch + line;
+    C v[V];
+
+    // stage 0 inputs straight from global memory
+    constexpr bool HZ0 = MODE != COL_INV;
+    constexpr int D0 = MODE == COL_INV ? +1 : -1;
+#pragma unroll
+    for (int k = 0; k < V / R1; ++k)
+#pragma unroll
+        for (int r = 0; r < (HZ0 ? R1 / 2 : R1); ++r) {
+            const int p = t + k * TPL + r * (n / R1);
+            v[k * R1 + r] = ok ? in[(long long)p * a.in_pos] : C{T(0), T(0)};
+        }
+    Stg<T, D0, n, V, L>::template compute<R1, 1, HZ0, false>(v, t, tw);
+    run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV>(v, buf, t, l, tw, false);
+
+    if constexpr (MODE == COL_FMI) {
+        // multiply by the real, even spectrum at the folded frequency
+        const T *S = reinterpret_cast<const T *>(a.S);
+        const int h2 = 2 * a.half;
+        const int fy = (int)bt <= a.half ? (int)bt : h2 - (int)bt;
+        const T *Sy = S + (long long)fy * a.s_batch + line;
+#pragma unroll
+        for (int k = 0; k < V / RL; ++k)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+                const int p = t + k * TPL + r * (n / RL);
+                const int fz = p <= a.half ? p : h2 - p;
+                const T s = ok ? Sy[(long long)fz * a.s_pos] : T(0);
+                v[k * RL + r].x *= s;
+                v[k * RL + r].y *= s;
+            }
+        // inverse, radix schedule reversed: its stage 0 is the forward's last
+        // radix on the same butterflies, already in registers
+        using SI = Stg<T, +1, n, V, L>;
+        if constexpr (R3 > 1) {
+            SI::template compute<R3, 1, false, false>(v, t, tw);
+            run_rest<T, +1, n, V, L, R3, R2, R1, true>(v, buf, t, l, tw, true);
+        } else {
+            SI::template compute<R2, 1, false, false>(v, t, tw);
+            run_rest<T, +1, n, V, L, R2, R1, 1, true>(v, buf, t, l, tw, true);
+        }
+        constexpr int RF = R1;  // last radix of the reversed schedule
+#pragma unroll
+        for (int k = 0; k < V / RF; ++k)
+#pragma unroll
+            for (int r = 0; r < RF / 2; ++r) {
+                const int p = t + k * TPL + r * (n / RF);
+                if (ok) out[(long long)p * a.out_pos] = v[k * RF + r];
+            }
+    } else {
+        constexpr bool HO = MODE == COL_INV;
+#pragma unroll
+        for (int k = 0; k < V / RL; ++k)
+#pragma unroll
+            for (int r = 0; r < (HO ? RL / 2 : RL); ++r) {
+                const int p = t + k * TPL + r * (n / RL);
+                if (ok) out[(long long)p * a.out_pos] = v[k * RL + r];
+            }
+    }
+}
+
+// ------------------------------------------------------- row kernels --
+// P1: rows of N reals -> N+1 coefficients of the zero-padded length-2N row,
+// through the length-N FFT of z[m] = x[2m] + i x[2m+1] (zero for m >= N/2).
+template <typename T, int N, int V, int L, int R1, int R2, int R3>
+__global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
+    using C = cx_t<T>;
+    constexpr int TPL = N / V, LD = L + 1, NTH = L * TPL, H = N / 2;
+    constexpr int RL = LastR<R1, R2, R3>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int tid = threadIdx.x, l = tid % L, t = tid / L;
+    const long long row0 = (long long)blockIdx.x * L;
+    const T *x = reinterpret_cast<const T *>(a.x);
+    // coalesced row loads of the packed pairs (x[2m], x[2m+1]), m < N/2
+#pragma unroll 4
+    for (int idx = tid; idx < L * H; idx += NTH) {
+        const int m = idx % H, rr = idx / H;
+        C z = C{T(0), T(0)};
+        if (row0 + rr < a.nrows) z = reinterpret_cast<const C *>(x + (row0 + rr) * a.x_row)[m];
+        buf[m * LD + rr] = z;
+    }
+    __syncthreads();
+    const C *tw = reinterpret_cast<const C *>(a.tw);
+    using S = Stg<T, -1, N, V, L>;
+    C v[V];
+#pragma unroll
+    for (int k = 0; k < V / R1; ++k)
+#pragma unroll
+        for (int r = 0; r < R1 / 2; ++r) v[k * R1 + r] = buf[(t + k * TPL + r * (N / R1)) * LD + l];
+    S::template compute<R1, 1, true, false>(v, t, tw);
+    run_rest<T, -1, N, V, L, R1, R2, R3, false>(v, buf, t, l, tw, true);
+    // natural-order spectrum Z back to shared memory
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < V / RL; ++k)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) buf[(t + k * TPL + r * (N / RL)) * LD + l] = v[k * RL + r];
+    __syncthreads();
+    // X[k] = E + w^k O, X[N-k] = conj(E - w^k O), E/O from Z[k], Z[N-k]
+    const C *tw2 = reinterpret_cast<const C *>(a.tw2);
+    for (int k = t; 2 * k <= N; k += TPL) {
+        const int kc = k == 0 ? 0 : N - k;
+        const C zk = buf[k * LD + l], zc = buf[kc * LD + l];
+        const C e = C{T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
+        const C o = C{T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
+        const C wo = cmul(__ldg(tw2 + k), o);
+        if (k == 0) {
+            buf[l] = cadd(e, o);
+            buf[N * LD + l] = csub(e, o);
+        } else {
+            buf[k * LD + l] = cadd(e, wo);
+            if (2 * k != N) buf[kc * LD + l] = cconj(csub(e, wo));
+        }
+    }
+    __syncthreads();
+    C *c = reinterpret_cast<C *>(a.c);
+    for (int idx = tid; idx < L * (N + 1); idx += NTH) {
+        const int k = idx % (N + 1), rr = idx / (N + 1);
+        if (row0 + rr < a.nrows) c[(row0 + rr) * a.c_row + k] = buf[k * LD + rr];
+    }
+}
+
+// P5: N+1 coefficients -> first N of the 2N real outputs.
+template <typename T, int N, int V, int L, int R1, int R2, int R3>
+__global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
+    using C = cx_t<T>;
+    constexpr int TPL = N / V, LD = L + 1, NTH = L * TPL, H = N / 2;
+    constexpr int RL = LastR<R1, R2, R3>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int tid = threadIdx.x, l = tid % L, t = tid / L;
+    const long long row0 = (long long)blockIdx.x * L;
+    const C *c = reinterpret_cast<const C *>(a.c);
+    for (int idx = tid; idx < L * (N + 1); idx += NTH) {
+        const int k = idx % (N + 1), rr = idx / (N + 1);
+        C val = C{T(0), T(0)};
+        if (row0 + rr < a.nrows) val = c[(row0 + rr) * a.c_row + k];
+        buf[k * LD + rr] = val;
+    }
+    __syncthreads();
+    // Z[k] = A + i conj(w^k) B, Z[N-k] = conj A + i w^k conj B
+    const C *tw2 = reinterpret_cast<const C *>(a.tw2);
+    for (int k = t; 2 * k <= N; k += TPL) {
+        const int kc = N - k;
+        const C xk = buf[k * LD + l], xc = buf[kc * LD + l];
+        const C A = C{xk.x + xc.x, xk.y - xc.y};
+        const C B = C{xk.x - xc.x, xk.y + xc.y};
+        const C w = __ldg(tw2 + k);
+        buf[k * LD + l] = cadd(A, cmuli(cmul(cconj(w), B)));
+        if (k != 0 && 2 * k != N) buf[kc * LD + l] = cadd(cconj(A), cmuli(cmul(w, cconj(B))));
+    }
+    __syncthreads();
+    const C *tw = reinterpret_cast<const C *>(a.tw);
+    using S = Stg<T, +1, N, V, L>;
+    C v[V];
+    S::template load_in<R1>(v, buf, t, l);
+    S::template compute<R1, 1, false, false>(v, t, tw);
+    run_rest<T, +1, N, V, L, R1, R2, R3, true>(v, buf, t, l, tw, true);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < V / RL; ++k)
+#pragma unroll
+        for (int r = 0; r < RL / 2; ++r) buf[(t + k * TPL + r * (N / RL)) * LD + l] = v[k * RL + r];
+    __syncthreads();
+    T *x = reinterpret_cast<T *>(const_cast<void *>(a.x));
+#pragma unroll 4
+    for (int idx = tid; idx < L * H; idx += NTH) {
+        const int m = idx % H, rr = idx / H;
+        if (row0 + rr < a.nrows) reinterpret_cast<C *>(x + (row0 + rr) * a.x_row)[m] = buf[m * LD + rr];
+    }
+}
+
+// ----------------------------------------------------- configurations --
+// Tile shape and radix schedule per (type, length); Ok = false: no fast path.
+template <typename T, int n> struct Cfg {
+    static constexpr bool Ok = false;
+    static constexpr int V = 8, L = 8, R1 = 8, R2 = 8, R3 = 1;
+};
+#define FSP_CFG(TT, NN, VV, LL, A, B, CC)                                   \
+    template <> struct Cfg<TT, NN> {                                       \
+        static constexpr bool Ok = true;                                   \
+        static constexpr int V = VV, L = LL, R1 = A, R2 = B, R3 = CC;      \
+    };
+FSP_CFG(float, 32, 8, 16, 4, 8, 1)
+FSP_CFG(float, 64, 8, 16, 8, 8, 1)
+FSP_CFG(float, 128, 16, 16, 8, 16, 1)
+FSP_CFG(float, 256, 16, 16, 16, 16, 1)
+FSP_CFG(float, 512, 32, 16, 16, 32, 1)
+FSP_CFG(float, 1024, 32, 8, 32, 32, 1)
+FSP_CFG(double, 32, 8, 16, 4, 8, 1)
+FSP_CFG(double, 64, 8, 16, 8, 8, 1)
+FSP_CFG(double, 128, 16, 8, 8, 16, 1)
+FSP_CFG(double, 256, 16, 8, 16, 16, 1)
+FSP_CFG(double, 512, 8, 8, 8, 8, 8)
+FSP_CFG(double, 1024, 16, 8, 16, 8, 8)
+#undef FSP_CFG
+
+template <typename T, int n> constexpr size_t smem_for(int positions) {
+    return (size_t)positions * (Cfg<T, n>::L + 1) * sizeof(cx_t<T>);
+}
+
+}  // namespace fast
+}  // namespace fsp
+
+// --------------------------------------------------------------- launchers
+namespace fsp {
+namespace fast {
+
+template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a, int nbatch, cudaStream_t s) {
+    using K = Cfg<T, n>;
+    if constexpr (!K::Ok) {
+        return cudaErrorInvalidValue;
+    } else {
+        auto kern = k_fast_col<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE>;
+        const size_t sm = smem_for<T, n>(n);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((a.nlines + K::L - 1) / K::L), (unsigned)nbatch);
+        kern<<<grid, K::L * (n / K::V), sm, s>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+template <typename T, int N, bool R2C> cudaError_t launch_row_n(const RowArgs &a, cudaStream_t s) {
+    using K = Cfg<T, N>;
+    if constexpr (!K::Ok) {
+        return cudaErrorInvalidValue;
+    } else {
+        auto kern = R2C ? k_fast_r2c<T, N, K::V, K::L, K::R1, K::R2, K::R3>
+                        : k_fast_c2r<T, N, K::V, K::L, K::R1, K::R2, K::R3>;
+        const size_t sm = smem_for<T, N>(N + 1);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)((a.nrows + K::L - 1) / K::L), K::L * (N / K::V), sm, s>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+template <typename T, int MODE> cudaError_t launch_col(int n, const ColArgs &a, int nbatch, cudaStream_t s) {
+    switch (n) {
+    case 64: return launch_col_n<T, 64, MODE>(a, nbatch, s);
+    case 128: return launch_col_n<T, 128, MODE>(a, nbatch, s);
+    case 256: return launch_col_n<T, 256, MODE>(a, nbatch, s);
+    case 512: return launch_col_n<T, 512, MODE>(a, nbatch, s);
+    case 1024: return launch_col_n<T, 1024, MODE>(a, nbatch, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, cudaStream_t s) {
+    switch (N) {
+    case 32: return launch_row_n<T, 32, R2C>(a, s);
+    case 64: return launch_row_n<T, 64, R2C>(a, s);
+    case 128: return launch_row_n<T, 128, R2C>(a, s);
+    case 256: return launch_row_n<T, 256, R2C>(a, s);
+    case 512: return launch_row_n<T, 512, R2C>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+#define FSP_FAST_INSTANTIATE(T)                                                                                \
+    template <> bool has<T>(int N) { return N == 32 || N == 64 || N == 128 || N == 256 || N == 512; }           \
+    template <> cudaError_t p1<T>(int N, const RowArgs &a, cudaStream_t s) { return launch_row<T, true>(N, a, s); } \
+    template <> cudaError_t p5<T>(int N, const RowArgs &a, cudaStream_t s) { return launch_row<T, false>(N, a, s); } \
+    template <> cudaError_t p2<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
+        return launch_col<T, COL_FWD>(2 * N, a, nb, s);                                                        \
+    }                                                                                                          \
+    template <> cudaError_t p3<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
+        return launch_col<T, COL_FMI>(2 * N, a, nb, s);                                                        \
+    }                                                                                                          \
+    template <> cudaError_t p4<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
+        return launch_col<T, COL_INV>(2 * N, a, nb, s);                                                        \
+    }
+
+}  // namespace fast
+}  // namespace fsp

@@ -1,0 +1,44 @@
+// fast.h -- host interface of the specialised power-of-two pass kernels
+// (fast.cuh): argument blocks and one launcher per solve pass.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fsp {
+namespace fast {
+
+// Column pass: line c of batch b, position p at base + b*batch + c + p*pos.
+struct ColArgs {
+    const void *in;
+    void *out;
+    long long in_pos, in_batch, out_pos, out_batch;
+    int nlines;
+    const void *tw;  // forward roots exp(-2 pi i e / n), n = 2N
+    const void *S;   // P3: real spectrum S[fold(p)*s_pos + fold(b)*s_batch + c]
+    long long s_pos, s_batch;
+    int half;        // N
+};
+
+// Row pass: rows of N reals (x, stride x_row) <-> rows of N+1 complex (c,
+// stride c_row).
+struct RowArgs {
+    const void *x;
+    void *c;
+    long long x_row, c_row;
+    int nrows;
+    const void *tw;   // roots of length N
+    const void *tw2;  // roots of length 2N
+};
+
+enum ColMode { COL_FWD = 0, COL_INV = 1, COL_FMI = 2 };
+
+// true when the specialised kernels cover this N (N = 32, 64, 128, 256, 512)
+template <typename T> bool has(int N);
+// P1 pad + x-R2C, P2 y-FFT, P3 z-FFT*S*z-IFFT, P4 y-IFFT, P5 x-C2R
+template <typename T> cudaError_t p1(int N, const RowArgs &a, cudaStream_t s);
+template <typename T> cudaError_t p2(int N, const ColArgs &a, int nbatch, cudaStream_t s);
+template <typename T> cudaError_t p3(int N, const ColArgs &a, int nbatch, cudaStream_t s);
+template <typename T> cudaError_t p4(int N, const ColArgs &a, int nbatch, cudaStream_t s);
+template <typename T> cudaError_t p5(int N, const RowArgs &a, cudaStream_t s);
+
+}  // namespace fast
+}  // namespace fsp

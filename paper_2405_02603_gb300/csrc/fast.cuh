@@ -325,6 +325,7 @@ template <typename T, int N, int V, int L, int R1, int R2, int R3>
 __global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
     using C = cx_t<T>;
     constexpr int TPL = N / V, LD = L + 1, NTH = L * TPL, H = N / 2;
+    static_assert(NTH % 32 == 0, "row kernels use whole warps per row");
     constexpr int RL = LastR<R1, R2, R3>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
@@ -373,10 +374,14 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
         }
     }
     __syncthreads();
+    // one warp per row: coalesced stores of the N+1 coefficients
     C *c = reinterpret_cast<C *>(a.c);
-    for (int idx = tid; idx < L * (N + 1); idx += NTH) {
-        const int k = idx % (N + 1), rr = idx / (N + 1);
-        if (row0 + rr < a.nrows) c[(row0 + rr) * a.c_row + k] = buf[k * LD + rr];
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int rr = warp; rr < L; rr += NTH / 32) {
+        if (row0 + rr < a.nrows) {
+            C *crow = c + (row0 + rr) * a.c_row;
+            for (int k = lane; k <= N; k += 32) crow[k] = buf[k * LD + rr];
+        }
     }
 }
 
@@ -390,12 +395,13 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int tid = threadIdx.x, l = tid % L, t = tid / L;
     const long long row0 = (long long)blockIdx.x * L;
+    // one warp per row: coalesced loads of the N+1 coefficients
     const C *c = reinterpret_cast<const C *>(a.c);
-    for (int idx = tid; idx < L * (N + 1); idx += NTH) {
-        const int k = idx % (N + 1), rr = idx / (N + 1);
-        C val = C{T(0), T(0)};
-        if (row0 + rr < a.nrows) val = c[(row0 + rr) * a.c_row + k];
-        buf[k * LD + rr] = val;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int rr = warp; rr < L; rr += NTH / 32) {
+        const bool okr = row0 + rr < a.nrows;
+        const C *crow = c + (row0 + rr) * a.c_row;
+        for (int k = lane; k <= N; k += 32) buf[k * LD + rr] = okr ? crow[k] : C{T(0), T(0)};
     }
     __syncthreads();
     // Z[k] = A + i conj(w^k) B, Z[N-k] = conj A + i w^k conj B

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace fsp {
 
 template <typename T> struct cx;
@@ -37,6 +39,16 @@ template <typename C> __device__ __forceinline__ C cmuli(C a) { return C{-a.y, a
 template <typename C> __device__ __forceinline__ C cmulmi(C a) { return C{a.y, -a.x}; }
 
 constexpr int kMaxV = 16;  // complex values a thread holds within one stage
+
+// Compile-time loop: f(integral_constant<int, I>) for I in [B, E).
+template <int B, int E> struct Unroll {
+    template <class F> static __device__ __forceinline__ void run(F &&f) {
+        if constexpr (B < E) {
+            f(std::integral_constant<int, B>{});
+            Unroll<B + 1, E>::run(f);
+        }
+    }
+};
 
 // Radix schedule of a length-n transform, always in the order: n5 radix-5
 // stages, n3 radix-3 stages, n8 radix-8 stages, then one radix-`last` stage
@@ -131,41 +143,55 @@ template <typename T, int D> struct Engine {
         return w;
     }
 
+    // The loops over butterflies and over the radix are unrolled by
+    // construction (Unroll), not by pragma: inside an outer loop (the
+    // persistent batched kernel) pragma unrolling is not guaranteed, and a
+    // partially unrolled loop would send the register array v to local memory.
     template <int R>
     static __device__ __forceinline__ void stage(C *buf, int ld, int n, int Ns, const C *__restrict__ tw, int l,
                                                  int sub, int tpl, bool act) {
         constexpr int KMAX = kMaxV / R;
         const int nb = n / R;
+        // Defined on entry: the loads below are predicated, and inside an outer
+        // loop an array that might be read before written stays live around
+        // the back-edge, so ptxas keeps every radix's array allocated at once.
         C v[KMAX * R];
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
+        Unroll<0, KMAX * R>::run([&](auto ic) { v[decltype(ic)::value] = C{T(0), T(0)}; });
+        Unroll<0, KMAX>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
             const int b = sub + k * tpl;
             if (act && b < nb) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[k * R + r] = buf[(b + r * nb) * ld + l];
+                Unroll<0, R>::run([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    v[k * R + r] = buf[(b + r * nb) * ld + l];
+                });
             }
-        }
+        });
         __syncthreads();
         const int tws = n / (Ns * R);
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
+        Unroll<0, KMAX>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
             const int b = sub + k * tpl;
             if (act && b < nb) {
                 const int j = b % Ns;
                 if (j != 0) {
-#pragma unroll
-                    for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], twid(tw, r * j * tws));
+                    Unroll<1, R>::run([&](auto rc) {
+                        constexpr int r = decltype(rc)::value;
+                        v[k * R + r] = cmul(v[k * R + r], twid(tw, r * j * tws));
+                    });
                 }
-                if (R == 2) Dft<T, D>::r2(v + k * R);
-                if (R == 3) Dft<T, D>::r3(v + k * R);
-                if (R == 4) Dft<T, D>::r4(v + k * R);
-                if (R == 5) Dft<T, D>::r5(v + k * R);
-                if (R == 8) Dft<T, D>::r8(v + k * R);
+                if constexpr (R == 2) Dft<T, D>::r2(v + k * R);
+                if constexpr (R == 3) Dft<T, D>::r3(v + k * R);
+                if constexpr (R == 4) Dft<T, D>::r4(v + k * R);
+                if constexpr (R == 5) Dft<T, D>::r5(v + k * R);
+                if constexpr (R == 8) Dft<T, D>::r8(v + k * R);
                 const int base = (b - j) * R + j;
-#pragma unroll
-                for (int r = 0; r < R; ++r) buf[(base + r * Ns) * ld + l] = v[k * R + r];
+                Unroll<0, R>::run([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    buf[(base + r * Ns) * ld + l] = v[k * R + r];
+                });
             }
-        }
+        });
         __syncthreads();
     }
 

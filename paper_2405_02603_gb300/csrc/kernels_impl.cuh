@@ -7,17 +7,27 @@ namespace fsp {
 
 constexpr int kMaxThreads = 512;
 
-// ---------------------------------------------------------------- k_lines --
-template <typename T, int IN, int OUT, int MODE>
-__global__ void __launch_bounds__(kMaxThreads) k_lines(const LinesArgs a) {
+// Loads of data another CTA of the same launch may have written (the
+// persistent batched kernel) bypass L1, which is not coherent across SMs.
+template <bool COH, typename V> __device__ __forceinline__ V ldw(const V *p) {
+    if constexpr (COH)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+// ---------------------------------------------------------- lines_tile --
+// One tile of a batched line transform: lines [bx*L, bx*L + L) of batch `by`.
+// Every thread of the CTA must call it (barriers); threads beyond L*tpl idle.
+template <typename T, int IN, int OUT, int MODE, bool COH>
+__device__ __forceinline__ void lines_tile(const LinesArgs &a, int bx, long long by, unsigned char *smem_raw) {
     using C = cx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int L = 1 << a.lgL, lmask = L - 1;
     const int ld = L + 1;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int line0 = blockIdx.x << a.lgL;
-    const long long b = blockIdx.y;
+    const int line0 = bx << a.lgL;
+    const long long b = by;
     const int n = a.st.n;
 
     // ---- load (with zero padding / even extension)
@@ -28,14 +38,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_lines(const LinesArgs a) {
             for (int idx = tid; idx < cnt; idx += nth) {
                 const int l = idx & lmask, p = idx >> a.lgL;
                 C v = C{T(0), T(0)};
-                if (line0 + l < a.nlines) v = in[(long long)(line0 + l) + (long long)p * a.in_pos];
+                if (line0 + l < a.nlines) v = ldw<COH>(in + ((long long)(line0 + l) + (long long)p * a.in_pos));
                 buf[p * ld + l] = v;
             }
         } else {
             for (int idx = tid; idx < cnt; idx += nth) {
                 const int p = idx % a.n_in, l = idx / a.n_in;
                 C v = C{T(0), T(0)};
-                if (line0 + l < a.nlines) v = in[(long long)(line0 + l) * a.in_line + (long long)p * a.in_pos];
+                if (line0 + l < a.nlines)
+                    v = ldw<COH>(in + ((long long)(line0 + l) * a.in_line + (long long)p * a.in_pos));
                 buf[p * ld + l] = v;
             }
         }
@@ -57,7 +68,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_lines(const LinesArgs a) {
                 l = idx / np;
             }
             T x = T(0);
-            if (line0 + l < a.nlines) x = in[(long long)(line0 + l) * a.in_line + (long long)p * a.in_pos];
+            if (line0 + l < a.nlines) x = ldw<COH>(in + ((long long)(line0 + l) * a.in_line + (long long)p * a.in_pos));
             buf[p * ld + l] = C{x, T(0)};
             if (p > 0 && p < M) buf[(n - p) * ld + l] = C{x, T(0)};
         }
@@ -65,7 +76,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_lines(const LinesArgs a) {
     __syncthreads();
 
     const int l = tid & lmask, sub = tid >> a.lgL;
-    const bool act = (line0 + l) < a.nlines;
+    const bool act = (line0 + l) < a.nlines && sub < a.tpl;
     const C *tw = reinterpret_cast<const C *>(a.tw);
     if (MODE == M_INV)
         Engine<T, +1>::run(buf, ld, a.st, tw, l, sub, a.tpl, act);
@@ -125,19 +136,25 @@ __global__ void __launch_bounds__(kMaxThreads) k_lines(const LinesArgs a) {
     }
 }
 
-// ------------------------------------------------------------ k_r2c_rows --
+template <typename T, int IN, int OUT, int MODE>
+__global__ void __launch_bounds__(kMaxThreads) k_lines(const LinesArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    lines_tile<T, IN, OUT, MODE, false>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// ------------------------------------------------------------ r2c_tile --
 // Sec. 2.2 steps 2 and 4 along x: each row of N reals, zero-padded to 2N, is
 // transformed to its N+1 non-redundant coefficients.  With z[m] = x[2m] +
 // i x[2m+1] (zero for 2m >= N) and Z = FFT_N(z):
 //   E = (Z[k] + conj Z[N-k]) / 2,  O = -i (Z[k] - conj Z[N-k]) / 2,
 //   X[k] = E + w^k O,  X[N-k] = conj(E - w^k O),  w = exp(-2 pi i / 2N).
-template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_r2c_rows(const RowsArgs a) {
+template <typename T, bool COH>
+__device__ __forceinline__ void r2c_tile(const RowsArgs &a, int bx, unsigned char *smem_raw) {
     using C = cx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int L = 1 << a.lgL, lmask = L - 1, ld = L + 1;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const long long row0 = (long long)blockIdx.x << a.lgL;
+    const long long row0 = (long long)bx << a.lgL;
     const int N = a.N, Mh = (N + 1) >> 1;
     const T *x = reinterpret_cast<const T *>(a.x);
 
@@ -148,10 +165,10 @@ template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_r2c_rows(
         if (row0 + l < a.nrows) {
             const T *xr = x + (row0 + l) * a.x_row;
             if ((N & 1) == 0) {
-                v = reinterpret_cast<const C *>(xr)[m];
+                v = ldw<COH>(reinterpret_cast<const C *>(xr) + m);
             } else {
-                v.x = xr[2 * m];
-                v.y = (2 * m + 1 < N) ? xr[2 * m + 1] : T(0);
+                v.x = ldw<COH>(xr + 2 * m);
+                v.y = (2 * m + 1 < N) ? ldw<COH>(xr + 2 * m + 1) : T(0);
             }
         }
         buf[m * ld + l] = v;
@@ -161,7 +178,7 @@ template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_r2c_rows(
     __syncthreads();
 
     const int l = tid & lmask, sub = tid >> a.lgL;
-    const bool act = (row0 + l) < a.nrows;
+    const bool act = (row0 + l) < a.nrows && sub < a.tpl;
     Engine<T, -1>::run(buf, ld, a.st, reinterpret_cast<const C *>(a.tw), l, sub, a.tpl, act);
 
     const C *tw2 = reinterpret_cast<const C *>(a.tw2);
@@ -191,19 +208,24 @@ template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_r2c_rows(
     }
 }
 
-// ------------------------------------------------------------ k_c2r_rows --
+template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_r2c_rows(const RowsArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    r2c_tile<T, false>(a, blockIdx.x, smem_raw);
+}
+
+// ------------------------------------------------------------ c2r_tile --
 // Sec. 2.2 steps 4 and 5 along x: from the N+1 coefficients X[k] of a real
 // length-2N signal y, y[j] = sum_k X[k] exp(+2 pi i jk / 2N), keep j < N.
 // With A = X[k] + conj X[N-k], B = X[k] - conj X[N-k], w = exp(-2 pi i/2N):
 //   Z[k] = A + i conj(w^k) B,  Z[N-k] = conj A + i w^k conj B,
 //   z = IFFT_N(Z) (unnormalised),  y[2m] = Re z[m],  y[2m+1] = Im z[m].
-template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_c2r_rows(const RowsArgs a) {
+template <typename T, bool COH>
+__device__ __forceinline__ void c2r_tile(const RowsArgs &a, int bx, unsigned char *smem_raw) {
     using C = cx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int L = 1 << a.lgL, ld = L + 1;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const long long row0 = (long long)blockIdx.x << a.lgL;
+    const long long row0 = (long long)bx << a.lgL;
     const int N = a.N, np = N + 1;
     const C *c = reinterpret_cast<const C *>(a.c);
 
@@ -211,13 +233,13 @@ template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_c2r_rows(
     for (int idx = tid; idx < cnt; idx += nth) {
         const int k = idx % np, l = idx / np;
         C v = C{T(0), T(0)};
-        if (row0 + l < a.nrows) v = c[(row0 + l) * a.c_row + k];
+        if (row0 + l < a.nrows) v = ldw<COH>(c + ((row0 + l) * a.c_row + k));
         buf[k * ld + l] = v;
     }
     __syncthreads();
 
     const int l = tid & (L - 1), sub = tid >> a.lgL;
-    const bool act = (row0 + l) < a.nrows;
+    const bool act = (row0 + l) < a.nrows && sub < a.tpl;
     const C *tw2 = reinterpret_cast<const C *>(a.tw2);
     if (act) {
         for (int k = sub; 2 * k <= N; k += a.tpl) {
@@ -248,6 +270,11 @@ template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_c2r_rows(
             }
         }
     }
+}
+
+template <typename T> __global__ void __launch_bounds__(kMaxThreads) k_c2r_rows(const RowsArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c2r_tile<T, false>(a, blockIdx.x, smem_raw);
 }
 
 // -------------------------------------------------------------- k_roots --

@@ -173,6 +173,82 @@ fsp_status fsp_kernel_T(int N, double L, fsp_algo algo, double *t_dev, fsp_strea
  */
 fsp_status fsp_fft_c2c(int n, int count, fsp_dtype dtype, int sign, const void *in, void *out, fsp_stream stream);
 
+/* ------------------------------------------------------------- batches --
+ * Many independent solves of mixed sizes in ONE persistent kernel launch,
+ * replayed as a CUDA graph (a systems form; the paper solves one grid at a
+ * time).  The launch walks a work list of tiles ordered pass by pass; a tile
+ * of pass p waits, on the device, for pass p-1 of its own solve.  Every such
+ * wait is bounded in time (default 1000 ms): when a limit runs out the kernel
+ * records FSP_ETIMEOUT, all blocks stop taking work and the launch ends, and
+ * fsp_batch_wait returns FSP_ETIMEOUT with the context still usable.
+ */
+typedef struct fsp_batch fsp_batch;
+
+/* Build a batch over `count` solves: plans[i] with device arrays rho[i] ->
+ * phi[i] (16-byte aligned, N_i^3 reals).  The plans must be distinct (each
+ * owns its workspace), live, of one dtype and on the current device; they
+ * must outlive the batch.  The work list and the graph are built once; each
+ * launch re-reads rho[i] and rewrites phi[i].  Every tile uses the generic
+ * mixed-radix engine with the plan's tile shapes, so a batched result is
+ * bitwise equal to a single solve through that engine (FSP_GENERIC_ONLY=1).
+ * Synchronises `stream`. */
+fsp_status fsp_batch_create(fsp_batch **out, fsp_plan *const *plans, const void *const *rho, void *const *phi,
+                            int count, fsp_stream stream);
+/* Launch the batch's graph on `stream` (asynchronous).  One launch of a batch
+ * may be in flight at a time. */
+fsp_status fsp_batch_launch(fsp_batch *batch, fsp_stream stream);
+/* Synchronise `stream` and return the last launch's device status: FSP_OK or
+ * FSP_ETIMEOUT. */
+fsp_status fsp_batch_wait(fsp_batch *batch, fsp_stream stream);
+/* Change the per-wait time limit (milliseconds, > 0); rebuilds the graph. */
+fsp_status fsp_batch_set_timeout(fsp_batch *batch, double ms);
+/* Fault injection for tests, made on the host: one dependency of the work
+ * list is raised by one tile that never exists, so that wait can only end by
+ * its time limit.  Later launches then end with FSP_ETIMEOUT. */
+fsp_status fsp_batch_inject_stall(fsp_batch *batch);
+fsp_status fsp_batch_destroy(fsp_batch *batch);
+/* create + launch + wait + destroy in one call. */
+fsp_status fsp_solve_batched(fsp_plan *const *plans, const void *const *rho, void *const *phi, int count,
+                             fsp_stream stream);
+
+/* -------------------------------------------------------------- server --
+ * Continuous-batching solve server (a systems form; no counterpart in the
+ * paper).  A worker thread owned by the server admits queued requests into
+ * free slots (one CUDA stream each) as soon as a slot and device memory are
+ * free, so solves of different sizes overlap on the device.  Spectra are
+ * cached per (N, L, algo, dtype) and evicted least-recently-used; spectra,
+ * workspaces and cached plans together never exceed the budget.  Every solve
+ * uses the same kernels as fsp_solve, so a result is bitwise the same alone
+ * or in a mix.  A cache miss builds the spectrum synchronously in the worker
+ * (other requests wait meanwhile).
+ */
+typedef struct fsp_server fsp_server;
+
+typedef struct {
+    uint64_t submitted, admitted, completed;
+    uint64_t spec_hits, spec_misses, evictions;
+    uint64_t queued, running;
+    uint64_t cached_spectra;
+    size_t bytes_in_use, budget;
+} fsp_server_stats;
+
+/* hbm_budget_bytes > 0; 1 <= max_slots <= 64 (concurrent solves). */
+fsp_status fsp_server_create(fsp_server **out, size_t hbm_budget_bytes, int max_slots);
+/* Queue one solve phi = G * rho (DEVICE arrays, 16-byte aligned, N^3 reals of
+ * dtype) on the server's device; h = L/N.  Sizes are validated now
+ * (FSP_EINVAL / FSP_EUNSUPPORTED); FSP_EBUSY when 65536 requests are queued.
+ * rho and phi must stay valid and untouched until the request is done. */
+fsp_status fsp_server_submit(fsp_server *server, int N, double L, fsp_algo algo, fsp_dtype dtype, const void *rho,
+                             void *phi, uint64_t *ticket);
+/* *state: 0 queued, 1 running, 2 done, 3 failed.  When done or failed,
+ * *latency_ms (may be NULL) is submit-to-completion wall time, the request is
+ * forgotten (a later poll of it returns FSP_EINVAL) and the return value is
+ * its status; otherwise FSP_OK. */
+fsp_status fsp_server_poll(fsp_server *server, uint64_t ticket, int *state, double *latency_ms);
+fsp_status fsp_server_get_stats(fsp_server *server, fsp_server_stats *out);
+/* Stops the worker, waits for the device, frees everything. */
+fsp_status fsp_server_destroy(fsp_server *server);
+
 /*
  * fsp_solve_noalloc -- an FP64 solve that allocates no device memory.  The
  * paper has no counterpart: it is an interface for callers that cannot call

@@ -24,6 +24,13 @@ DTYPES = {"f64": 0, "f32": 1}
 _lib = None
 
 
+class ServerStats(ctypes.Structure):
+    """fsp_server_stats"""
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "spec_hits", "spec_misses",
+                                               "evictions", "queued", "running", "cached_spectra")] + \
+               [("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t)]
+
+
 class FspError(RuntimeError):
     """A non-FSP_OK status returned by the library."""
 
@@ -67,6 +74,26 @@ def lib(build_if_missing=True):
     L.fsp_solve_noalloc.argtypes = [i, vp, vp, vp, vp]
     L.fsp_plan_uses_fast_path.argtypes = [vp]
     L.fsp_plan_uses_fast_path.restype = i
+    vpp = ctypes.POINTER(vp)
+    L.fsp_batch_create.argtypes = [vpp, vpp, vpp, vpp, i, vp]
+    L.fsp_batch_launch.argtypes = [vp, vp]
+    L.fsp_batch_wait.argtypes = [vp, vp]
+    L.fsp_batch_set_timeout.argtypes = [vp, d]
+    L.fsp_batch_inject_stall.argtypes = [vp]
+    L.fsp_batch_destroy.argtypes = [vp]
+    L.fsp_solve_batched.argtypes = [vpp, vpp, vpp, i, vp]
+    u64 = ctypes.c_uint64
+    L.fsp_server_create.argtypes = [vpp, ctypes.c_size_t, i]
+    L.fsp_server_submit.argtypes = [vp, i, d, i, i, vp, vp, ctypes.POINTER(u64)]
+    L.fsp_server_poll.argtypes = [vp, u64, ctypes.POINTER(i), ctypes.POINTER(d)]
+    L.fsp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.fsp_server_destroy.argtypes = [vp]
+    for name in ("fsp_server_create", "fsp_server_submit", "fsp_server_poll", "fsp_server_get_stats",
+                 "fsp_server_destroy"):
+        getattr(L, name).restype = i
+    for name in ("fsp_batch_create", "fsp_batch_launch", "fsp_batch_wait", "fsp_batch_set_timeout",
+                 "fsp_batch_inject_stall", "fsp_batch_destroy", "fsp_solve_batched"):
+        getattr(L, name).restype = i
     for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
                  "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc"):
         getattr(L, name).restype = i
@@ -195,6 +222,128 @@ def kernel_T(N, L=1.0, algo="vg_dct", stream=None):
     return t
 
 
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[ctypes.c_void_p(x) for x in xs])
+
+
+class Batch:
+    """Many solves of mixed N in one persistent launch, replayed as a CUDA graph
+    (fsp_batch_create / fsp_batch_launch / fsp_batch_wait)."""
+
+    def __init__(self, plans, rhos, phis, stream=None):
+        if not (len(plans) == len(rhos) == len(phis)) or not plans:
+            raise FspError(FSP_EINVAL, "Batch wants equal, non-empty lists")
+        for p, r, f in zip(plans, rhos, phis):
+            p._check_tensor(r)
+            p._check_tensor(f)
+        self.plans, self.rhos, self.phis = list(plans), list(rhos), list(phis)  # keep them alive
+        self._b = ctypes.c_void_p()
+        check(lib().fsp_batch_create(ctypes.byref(self._b), _ptr_array([p.handle.value for p in plans]),
+                                     _ptr_array([r.data_ptr() for r in rhos]), _ptr_array([f.data_ptr() for f in phis]),
+                                     len(plans), _stream_handle(stream)), "fsp_batch_create")
+
+    def launch(self, stream=None):
+        check(lib().fsp_batch_launch(self._b, _stream_handle(stream)), "fsp_batch_launch")
+
+    def wait(self, stream=None):
+        """Synchronise and return the device status (FSP_OK or FSP_ETIMEOUT)."""
+        return int(lib().fsp_batch_wait(self._b, _stream_handle(stream)))
+
+    def set_timeout(self, ms):
+        check(lib().fsp_batch_set_timeout(self._b, float(ms)), "fsp_batch_set_timeout")
+
+    def inject_stall(self):
+        check(lib().fsp_batch_inject_stall(self._b), "fsp_batch_inject_stall")
+
+    def close(self):
+        if self._b is not None and self._b.value:
+            check(lib().fsp_batch_destroy(self._b), "fsp_batch_destroy")
+        self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(plans, rhos, phis, stream=None):
+    """fsp_solve_batched: create, launch, wait and destroy a batch."""
+    check(lib().fsp_solve_batched(_ptr_array([p.handle.value for p in plans]), _ptr_array([r.data_ptr() for r in rhos]),
+                                  _ptr_array([f.data_ptr() for f in phis]), len(plans), _stream_handle(stream)),
+          "fsp_solve_batched")
+    return phis
+
+
+class Server:
+    """Continuous-batching solve server (fsp_server_*): submit requests of any
+    size; a worker thread in the library admits them into free slots as slots
+    and the device-memory budget allow, with spectra cached per
+    (N, L, algo, dtype)."""
+
+    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, budget_bytes=100 << 30, max_slots=8):
+        self._v = ctypes.c_void_p()
+        check(lib().fsp_server_create(ctypes.byref(self._v), int(budget_bytes), int(max_slots)), "fsp_server_create")
+        self._keep = {}
+
+    def submit(self, rho, phi, L=1.0, algo="he", dtype="f32"):
+        """Queue phi = G * rho (CUDA tensors of N^3 values); returns a ticket."""
+        import torch
+        N = round(rho.numel() ** (1.0 / 3.0))
+        want = torch_dtype(dtype)
+        for t in (rho, phi):
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == want and t.numel() == N ** 3):
+                raise FspError(FSP_EINVAL, "Server.submit wants contiguous CUDA %s tensors of N^3 values" % want)
+        tk = ctypes.c_uint64()
+        check(lib().fsp_server_submit(self._v, int(N), float(L), _algo_code(algo), _dtype_code(dtype),
+                                      ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                                      ctypes.byref(tk)), "fsp_server_submit")
+        self._keep[tk.value] = (rho, phi)
+        return tk.value
+
+    def poll(self, ticket):
+        """(state, latency_ms, status); a finished ticket is reported once."""
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        rc = lib().fsp_server_poll(self._v, ctypes.c_uint64(ticket), ctypes.byref(st), ctypes.byref(lat))
+        if rc == FSP_EINVAL and ticket not in self._keep:
+            raise FspError(rc, "fsp_server_poll: unknown ticket")
+        if st.value >= self.DONE:
+            self._keep.pop(ticket, None)
+        return st.value, lat.value, rc
+
+    def wait(self, ticket, timeout_s=120.0):
+        """Busy-poll until the ticket finishes; returns its latency in ms."""
+        import time
+        t0 = time.perf_counter()
+        while True:
+            state, lat, rc = self.poll(ticket)
+            if state >= self.DONE:
+                check(rc, "server request")
+                return lat
+            if time.perf_counter() - t0 > timeout_s:
+                raise FspError(FSP_ETIMEOUT, "Server.wait")
+            time.sleep(0)
+
+    def stats(self):
+        s = ServerStats()
+        check(lib().fsp_server_get_stats(self._v, ctypes.byref(s)), "fsp_server_get_stats")
+        return {name: int(getattr(s, name)) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._v is not None and self._v.value:
+            check(lib().fsp_server_destroy(self._v), "fsp_server_destroy")
+        self._v = None
+        self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def solve_noalloc(S, rho, phi, stream=None):
     """FP64 solve for N <= 32 with no device allocation (fsp_solve_noalloc).
 
@@ -229,4 +378,4 @@ def fft_c2c(x, sign=-1, stream=None):
     return out
 
 
-__all__ = ["Plan", "FspError", "kernel_T", "fft_c2c", "solve_noalloc", "lib", "check", "library_path", "ALGOS", "DTYPES"]
+__all__ = ["Plan", "Batch", "Server", "solve_batched", "FspError", "kernel_T", "fft_c2c", "solve_noalloc", "lib", "check", "library_path", "ALGOS", "DTYPES"]

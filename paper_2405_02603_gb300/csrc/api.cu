@@ -2,17 +2,24 @@
 // the plan-time Green's spectrum pipeline and the five-pass solve.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <tuple>
 #include <unordered_set>
+#include <vector>
 
 #include "../../include/fsp.h"
+#include "batch.h"
 #include "fast.h"
 #include "greens.h"
 #include "kernels.cuh"
@@ -282,28 +289,29 @@ void plan_free(fsp_plan *p) {
     delete p;
 }
 
-template <typename T> cudaError_t enqueue_solve_fast(const fsp_plan *p, const void *rho, void *phi, cudaStream_t s) {
+template <typename T>
+cudaError_t enqueue_solve_fast(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
     const int N = p->N;
     const long long P = p->P;
     cudaError_t e;
     auto mark = [&](int i) { return p->timing ? cudaEventRecord(p->ev[i], s) : cudaSuccess; };
     fast::RowArgs r{};
-    r.x = rho, r.c = p->W1, r.x_row = N, r.c_row = P, r.nrows = N * N, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    r.x = rho, r.c = W1, r.x_row = N, r.c_row = P, r.nrows = N * N, r.tw = p->tw_n, r.tw2 = p->tw_2n;
     fast::ColArgs a{};
     a.tw = p->tw_2n, a.nlines = N + 1;
     if ((e = mark(0)) != cudaSuccess) return e;
     if ((e = fast::p1<T>(N, r, s)) != cudaSuccess) return e;  // P1: pad + x-R2C
     if ((e = mark(1)) != cudaSuccess) return e;
-    a.in = p->W1, a.out = p->W2;  // P2: y-FFT, W1[z][y][kx] -> W2[z][ky][kx]
+    a.in = W1, a.out = W2;  // P2: y-FFT, W1[z][y][kx] -> W2[z][ky][kx]
     a.in_pos = P, a.in_batch = (long long)N * P, a.out_pos = P, a.out_batch = 2LL * N * P;
     if ((e = fast::p2<T>(N, a, N, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    a.in = a.out = p->W2;  // P3: z-FFT * S * z-IFFT, in place, batch ky
+    a.in = a.out = W2;  // P3: z-FFT * S * z-IFFT, in place, batch ky
     a.in_pos = a.out_pos = 2LL * N * P, a.in_batch = a.out_batch = P;
     a.S = p->S, a.s_pos = (long long)(N + 1) * P, a.s_batch = P, a.half = N;
     if ((e = fast::p3<T>(N, a, 2 * N, s)) != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    a.in = p->W2, a.out = p->W1;  // P4: y-IFFT, W2 -> W1 (y < N)
+    a.in = W2, a.out = W1;  // P4: y-IFFT, W2 -> W1 (y < N)
     a.in_pos = P, a.in_batch = 2LL * N * P, a.out_pos = P, a.out_batch = (long long)N * P;
     if ((e = fast::p4<T>(N, a, N, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
@@ -312,7 +320,8 @@ template <typename T> cudaError_t enqueue_solve_fast(const fsp_plan *p, const vo
     return mark(5);
 }
 
-template <typename T> cudaError_t enqueue_solve_generic(const fsp_plan *p, const void *rho, void *phi, cudaStream_t s) {
+template <typename T>
+cudaError_t enqueue_solve_generic(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
     const int N = p->N;
     const long long P = p->P;
     cudaError_t e;
@@ -320,28 +329,28 @@ template <typename T> cudaError_t enqueue_solve_generic(const fsp_plan *p, const
     // P1: pad + x-R2C (rows of rho -> W1[z][y][kx])
     if ((e = mark(0)) != cudaSuccess) return e;
     RowsArgs r{};
-    r.x = rho, r.c = p->W1, r.x_row = N, r.c_row = P, r.N = N, r.nrows = N * N;
+    r.x = rho, r.c = W1, r.x_row = N, r.c_row = P, r.N = N, r.nrows = N * N;
     r.lgL = p->row.lgL, r.tpl = p->row.tpl, r.st = p->row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
     if ((e = launch_r2c_rows<T>(r, s)) != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
     // P2: y-FFT (columns kx of W1[z][y][.], y < N zero-padded to 2N) -> W2[z][ky][kx]
     LinesArgs a{};
     a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_2n;
-    a.in = p->W1, a.out = p->W2;
+    a.in = W1, a.out = W2;
     a.in_pos = P, a.in_line = 1, a.in_batch = (long long)N * P;
     a.out_pos = P, a.out_line = 1, a.out_batch = 2LL * N * P;
     a.n_in = N, a.n_out = 2 * N, a.nlines = N + 1, a.nbatch = N;
     if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD>(a, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
     // P3: z-FFT, multiply by S, z-IFFT, keep z < N (in place in W2, batch ky)
-    a.in = a.out = p->W2;
+    a.in = a.out = W2;
     a.in_pos = a.out_pos = 2LL * N * P, a.in_batch = a.out_batch = P;
     a.n_in = N, a.n_out = N, a.nbatch = 2 * N;
     a.S = p->S, a.s_pos = (long long)(N + 1) * P, a.s_batch = P, a.half = N;
     if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD_MUL_INV>(a, s)) != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
     // P4: y-IFFT, keep y < N: W2[z][ky][kx] -> W1[z][y][kx]
-    a.in = p->W2, a.out = p->W1;
+    a.in = W2, a.out = W1;
     a.in_pos = P, a.in_batch = 2LL * N * P;
     a.out_pos = P, a.out_batch = (long long)N * P;
     a.n_in = 2 * N, a.n_out = N, a.nbatch = N;
@@ -351,6 +360,15 @@ template <typename T> cudaError_t enqueue_solve_generic(const fsp_plan *p, const
     r.x = phi;
     if ((e = launch_c2r_rows<T>(r, s)) != cudaSuccess) return e;
     return mark(5);
+}
+
+// One solve of plan p with the given workspace (W1: N*N*P, W2: 2*N*N*P complex).
+cudaError_t enqueue_solve_ws(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
+    if (p->fast)
+        return p->dtype == FSP_F64 ? enqueue_solve_fast<double>(p, rho, phi, W1, W2, s)
+                                   : enqueue_solve_fast<float>(p, rho, phi, W1, W2, s);
+    return p->dtype == FSP_F64 ? enqueue_solve_generic<double>(p, rho, phi, W1, W2, s)
+                               : enqueue_solve_generic<float>(p, rho, phi, W1, W2, s);
 }
 
 }  // namespace
@@ -370,8 +388,11 @@ const char *fsp_status_str(fsp_status s) {
     return "FSP_?: unknown status";
 }
 
-fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo algo, fsp_dtype dtype,
-                           fsp_stream stream) {
+}  // extern "C"
+
+namespace {
+fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo algo, fsp_dtype dtype,
+                            fsp_stream stream, bool with_workspace) {
     if (!out) return FSP_EINVAL;
     *out = nullptr;
     fsp_status st = validate_size(N, L, algo);
@@ -412,13 +433,13 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
     const size_t w1 = (size_t)N * N * p->P * csize, w2 = 2 * w1;
     DevBuf bS, bW1, bW2, bt1, bt2;
     if ((st = alloc_or_nomem(bS, sbytes)) != FSP_OK) return fail(st);
-    if ((st = alloc_or_nomem(bW1, w1)) != FSP_OK) return fail(st);
-    if ((st = alloc_or_nomem(bW2, w2)) != FSP_OK) return fail(st);
+    if (with_workspace && (st = alloc_or_nomem(bW1, w1)) != FSP_OK) return fail(st);
+    if (with_workspace && (st = alloc_or_nomem(bW2, w2)) != FSP_OK) return fail(st);
     if ((st = alloc_or_nomem(bt1, csize * N)) != FSP_OK) return fail(st);
     if ((st = alloc_or_nomem(bt2, csize * 2 * N)) != FSP_OK) return fail(st);
     p->S = bS.release(), p->W1 = bW1.release(), p->W2 = bW2.release();
     p->tw_n = bt1.release(), p->tw_2n = bt2.release();
-    p->bytes = sbytes + w1 + w2 + csize * 3 * N;
+    p->bytes = sbytes + (with_workspace ? w1 + w2 : 0) + csize * 3 * N;
     cudaError_t e;
     if (dtype == FSP_F64) {
         e = launch_roots<double>(p->tw_n, N, s);
@@ -451,6 +472,14 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
     *out = p;
     return FSP_OK;
 }
+}  // namespace
+
+extern "C" {
+
+fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo algo, fsp_dtype dtype,
+                           fsp_stream stream) {
+    return plan_create_impl(out, N, L, h, algo, dtype, stream, true);
+}
 
 fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stream) {
     if (!plan_live(plan)) return FSP_EINVAL;
@@ -459,13 +488,8 @@ fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stre
     if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
     if (dev != plan->device) return FSP_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    if (plan->fast)
-        e = plan->dtype == FSP_F64 ? enqueue_solve_fast<double>(plan, rho, phi, s)
-                                   : enqueue_solve_fast<float>(plan, rho, phi, s);
-    else
-        e = plan->dtype == FSP_F64 ? enqueue_solve_generic<double>(plan, rho, phi, s)
-                                   : enqueue_solve_generic<float>(plan, rho, phi, s);
+    if (!plan->W1) return FSP_EINVAL;  // a spectrum-only plan (server cache) has no workspace
+    const cudaError_t e = enqueue_solve_ws(plan, rho, phi, plan->W1, plan->W2, s);
     return cuda_status(e);
 }
 
@@ -600,3 +624,588 @@ fsp_status fsp_fft_c2c(int n, int count, fsp_dtype dtype, int sign, const void *
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- batches --
+struct fsp_batch {
+    uint64_t magic = 0;
+    int device = 0, count = 0;
+    fsp_dtype dtype = FSP_F64;
+    std::vector<BatchSolve> solves;
+    std::vector<BatchSeg> segs;
+    int total = 0;
+    BatchSolve *d_solves = nullptr;
+    BatchSeg *d_segs = nullptr;
+    BatchCtl *d_ctl = nullptr;
+    size_t ctl_bytes = 0;
+    BatchLaunch launch{};
+    double timeout_ms = 1000.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr uint64_t kBatchMagic = 0x46535042'41544348ULL;  // "FSPBATCH"
+std::unordered_set<const fsp_batch *> g_batches;
+
+bool batch_live(const fsp_batch *b) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return b && g_batches.count(b) && b->magic == kBatchMagic;
+}
+
+void batch_free(fsp_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (void *q : {(void *)b->d_solves, (void *)b->d_segs, (void *)b->d_ctl})
+        if (q) cudaFree(q);
+    b->magic = 0;
+    delete b;
+}
+
+// Fill the device-side descriptor of one solve from its plan (generic engine
+// tile shapes; workspace reads through L2).
+BatchSolve batch_solve_of(const fsp_plan *p, const void *rho, void *phi) {
+    const int N = p->N;
+    const long long P = p->P;
+    BatchSolve b{};
+    RowsArgs r{};
+    r.c = p->W1, r.x_row = N, r.c_row = P, r.N = N, r.nrows = N * N;
+    r.lgL = p->row.lgL, r.tpl = p->row.tpl, r.st = p->row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    b.r1 = r, b.r5 = r;
+    b.r1.x = rho;
+    b.r5.x = phi;
+    LinesArgs a{};
+    a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_2n;
+    a.nlines = N + 1;
+    LinesArgs c2 = a;
+    c2.in = p->W1, c2.out = p->W2;
+    c2.in_pos = P, c2.in_line = 1, c2.in_batch = (long long)N * P;
+    c2.out_pos = P, c2.out_line = 1, c2.out_batch = 2LL * N * P;
+    c2.n_in = N, c2.n_out = 2 * N, c2.nbatch = N;
+    LinesArgs c3 = a;
+    c3.in = c3.out = p->W2;
+    c3.in_pos = c3.out_pos = 2LL * N * P, c3.in_line = c3.out_line = 1, c3.in_batch = c3.out_batch = P;
+    c3.n_in = N, c3.n_out = N, c3.nbatch = 2 * N;
+    c3.S = p->S, c3.s_pos = (long long)(N + 1) * P, c3.s_batch = P, c3.half = N;
+    LinesArgs c4 = a;
+    c4.in = p->W2, c4.out = p->W1;
+    c4.in_pos = P, c4.in_line = 1, c4.in_batch = 2LL * N * P;
+    c4.out_pos = P, c4.out_line = 1, c4.out_batch = (long long)N * P;
+    c4.n_in = 2 * N, c4.n_out = N, c4.nbatch = N;
+    b.c2 = c2, b.c3 = c3, b.c4 = c4;
+    b.ntx = (N + 1 + (1 << p->col.lgL) - 1) >> p->col.lgL;
+    const int ntr = (N * N + (1 << p->row.lgL) - 1) >> p->row.lgL;
+    b.ntiles[0] = ntr, b.ntiles[1] = b.ntx * N, b.ntiles[2] = b.ntx * 2 * N, b.ntiles[3] = b.ntx * N, b.ntiles[4] = ntr;
+    return b;
+}
+
+fsp_status batch_build_graph(fsp_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec), b->exec = nullptr;
+    if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
+    b->launch.timeout_ns = (unsigned long long)(b->timeout_ms * 1e6);
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return FSP_ECUDA;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = cudaMemsetAsync(b->d_ctl, 0, b->ctl_bytes, cs);
+        cudaError_t e2 = e1 == cudaSuccess ? (b->dtype == FSP_F64 ? launch_batch_kernel<double>(b->launch, cs)
+                                                                  : launch_batch_kernel<float>(b->launch, cs))
+                                           : e1;
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" fsp_status fsp_batch_create(fsp_batch **out, fsp_plan *const *plans, const void *const *rho,
+                                       void *const *phi, int count, fsp_stream stream) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !plans || !rho || !phi) return FSP_EINVAL;
+    std::unordered_set<const fsp_plan *> seen;
+    for (int i = 0; i < count; ++i) {
+        if (!plan_live(plans[i]) || !seen.insert(plans[i]).second) return FSP_EINVAL;  // distinct live plans
+        if (plans[i]->dtype != plans[0]->dtype || plans[i]->device != plans[0]->device) return FSP_EINVAL;
+        if (!rho[i] || !phi[i] || !aligned16(rho[i]) || !aligned16(phi[i])) return FSP_EINVAL;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    if (dev != plans[0]->device) return FSP_EINVAL;
+    fsp_batch *b = new fsp_batch();
+    b->device = dev, b->count = count, b->dtype = plans[0]->dtype;
+    const size_t csize = 2 * plans[0]->rsize;
+    int threads = 32;
+    size_t smem = 0;
+    for (int i = 0; i < count; ++i) {
+        const fsp_plan *p = plans[i];
+        b->solves.push_back(batch_solve_of(p, rho[i], phi[i]));
+        threads = std::max(threads, std::max((1 << p->row.lgL) * p->row.tpl, (1 << p->col.lgL) * p->col.tpl));
+        smem = std::max(smem, std::max((size_t)(p->N + 1) * ((1 << p->row.lgL) + 1) * csize,
+                                       (size_t)(2 * p->N) * ((1 << p->col.lgL) + 1) * csize));
+    }
+    threads = (threads + 31) / 32 * 32;
+    // pass-major work list; within a pass, larger solves first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return plans[x]->N > plans[y]->N; });
+    int first = 0;
+    for (int pass = 0; pass < 5; ++pass)
+        for (int i : order) {
+            BatchSeg g{};
+            g.solve = i, g.pass = pass, g.first = first, g.ntiles = b->solves[i].ntiles[pass];
+            g.need_prev = pass ? b->solves[i].ntiles[pass - 1] : 0;
+            first += g.ntiles;
+            b->segs.push_back(g);
+        }
+    b->total = first;
+    auto fail = [&](fsp_status st) {
+        batch_free(b);
+        return st;
+    };
+    b->ctl_bytes = sizeof(BatchCtl) + sizeof(int) * (5 * (size_t)count);
+    DevBuf ds, dg, dc;
+    fsp_status st;
+    if ((st = alloc_or_nomem(ds, sizeof(BatchSolve) * count)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(dg, sizeof(BatchSeg) * b->segs.size())) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(dc, b->ctl_bytes)) != FSP_OK) return fail(st);
+    b->d_solves = (BatchSolve *)ds.release(), b->d_segs = (BatchSeg *)dg.release(), b->d_ctl = (BatchCtl *)dc.release();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(b->d_solves, b->solves.data(), sizeof(BatchSolve) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_segs, b->segs.data(), sizeof(BatchSeg) * b->segs.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(FSP_ECUDA);
+    const int per_sm = b->dtype == FSP_F64 ? batch_blocks_per_sm<double>(threads, smem) : batch_blocks_per_sm<float>(threads, smem);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1 || sms < 1) return fail(FSP_EUNSUPPORTED);
+    b->launch.solves = b->d_solves, b->launch.segs = b->d_segs, b->launch.nseg = (int)b->segs.size();
+    b->launch.total = b->total, b->launch.ctl = b->d_ctl;
+    b->launch.grid = (unsigned)std::min<long long>((long long)sms * per_sm, b->total);
+    b->launch.threads = threads, b->launch.smem = smem;
+    if ((st = batch_build_graph(b)) != FSP_OK) return fail(st);
+    b->magic = kBatchMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_batches.insert(b);
+    }
+    *out = b;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_batch_launch(fsp_batch *b, fsp_stream stream) {
+    if (!batch_live(b)) return FSP_EINVAL;
+    return cuda_status(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" fsp_status fsp_batch_wait(fsp_batch *b, fsp_stream stream) {
+    if (!batch_live(b)) return FSP_EINVAL;
+    if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FSP_ECUDA;
+    int status = 0;
+    if (cudaMemcpy(&status, &b->d_ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FSP_ECUDA;
+    return status == 0 ? FSP_OK : (fsp_status)status;
+}
+
+extern "C" fsp_status fsp_batch_set_timeout(fsp_batch *b, double ms) {
+    if (!batch_live(b) || !(ms > 0.0) || ms > 3.6e6) return FSP_EINVAL;
+    b->timeout_ms = ms;
+    return batch_build_graph(b);
+}
+
+extern "C" fsp_status fsp_batch_inject_stall(fsp_batch *b) {
+    if (!batch_live(b)) return FSP_EINVAL;
+    // the last segment of pass 1 waits for one more pass-0 tile than exists
+    for (int i = (int)b->segs.size() - 1; i >= 0; --i)
+        if (b->segs[i].pass == 1) {
+            b->segs[i].need_prev += 1;
+            break;
+        }
+    if (cudaMemcpy(b->d_segs, b->segs.data(), sizeof(BatchSeg) * b->segs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FSP_ECUDA;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_batch_destroy(fsp_batch *b) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!b || !g_batches.count(b)) return FSP_EINVAL;
+        g_batches.erase(b);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    batch_free(b);
+    return cuda_status(e);
+}
+
+extern "C" fsp_status fsp_solve_batched(fsp_plan *const *plans, const void *const *rho, void *const *phi, int count,
+                                        fsp_stream stream) {
+    fsp_batch *b = nullptr;
+    fsp_status st = fsp_batch_create(&b, plans, rho, phi, count, stream);
+    if (st != FSP_OK) return st;
+    st = fsp_batch_launch(b, stream);
+    fsp_status w = fsp_batch_wait(b, stream);
+    fsp_batch_destroy(b);
+    return st != FSP_OK ? st : w;
+}
+
+// -------------------------------------------------------------- server --
+// Continuous batching: a worker thread owned by the server retires finished
+// solves and admits queued requests into free slots (one CUDA stream each)
+// whenever the device-memory budget allows, so that requests arriving while
+// others run start as soon as a slot and memory free up, and their kernels
+// overlap on the device.  Spectra are cached per (N, L, algo, dtype) (a plan
+// without workspace) and evicted least-recently-used when the budget needs
+// room; workspaces are pooled per (N, dtype).
+struct fsp_server {
+    uint64_t magic = 0;
+    int device = 0;
+    size_t budget = 0, used = 0;
+    int max_slots = 0, max_queue = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    std::thread worker;
+    struct Req {
+        int N;
+        double L;
+        fsp_algo algo;
+        fsp_dtype dtype;
+        const void *rho;
+        void *phi;
+        std::chrono::steady_clock::time_point t_submit, t_done;
+        int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+        fsp_status status = FSP_OK;
+    };
+    std::unordered_map<uint64_t, Req> reqs;
+    std::deque<uint64_t> queue;
+    uint64_t next_ticket = 1;
+    struct Spec {
+        fsp_plan *plan = nullptr;
+        size_t bytes = 0;
+        uint64_t last_use = 0;
+        int refs = 0;
+    };
+    std::map<std::tuple<int, uint64_t, int, int>, Spec> specs;
+    struct WS {
+        void *W1 = nullptr, *W2 = nullptr;
+        size_t bytes = 0;
+        int N = 0;
+        fsp_dtype dtype = FSP_F64;
+    };
+    std::vector<WS> idle_ws;
+    struct Slot {
+        cudaStream_t stream = nullptr;
+        cudaEvent_t ev = nullptr;
+        bool busy = false;
+        uint64_t ticket = 0;
+        WS ws;
+        std::tuple<int, uint64_t, int, int> key;
+    };
+    std::vector<Slot> slots;
+    uint64_t clock = 0;
+    fsp_server_stats st{};
+};
+
+namespace {
+
+constexpr uint64_t kServerMagic = 0x46535053'45525645ULL;  // "FSPSERVE"
+std::unordered_set<const fsp_server *> g_servers;
+
+bool server_live(const fsp_server *v) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return v && g_servers.count(v) && v->magic == kServerMagic;
+}
+
+uint64_t bits_of(double x) {
+    uint64_t u;
+    std::memcpy(&u, &x, sizeof(u));
+    return u;
+}
+
+size_t ws_bytes(int N, fsp_dtype dtype) {
+    const size_t P = ((N + 1) + 15) / 16 * 16;
+    return (size_t)N * N * P * (dtype == FSP_F64 ? 16 : 8) * 3;
+}
+
+// Free idle workspaces, then unreferenced spectra (least recently used first),
+// until `need` more bytes fit in the budget.  Caller holds v->mu.
+bool server_make_room(fsp_server *v, size_t need) {
+    while (v->used + need > v->budget && !v->idle_ws.empty()) {
+        fsp_server::WS w = v->idle_ws.back();
+        v->idle_ws.pop_back();
+        cudaFree(w.W1);
+        cudaFree(w.W2);
+        v->used -= w.bytes;
+    }
+    while (v->used + need > v->budget) {
+        auto victim = v->specs.end();
+        for (auto it = v->specs.begin(); it != v->specs.end(); ++it)
+            if (it->second.refs == 0 && (victim == v->specs.end() || it->second.last_use < victim->second.last_use))
+                victim = it;
+        if (victim == v->specs.end()) return false;
+        fsp_plan_destroy(victim->second.plan);
+        v->used -= victim->second.bytes;
+        v->specs.erase(victim);
+        v->st.evictions++;
+    }
+    return true;
+}
+
+void server_loop(fsp_server *v) {
+    cudaSetDevice(v->device);
+    std::unique_lock<std::mutex> lk(v->mu);
+    while (!v->stop) {
+        bool progress = false, running = false;
+        // retire finished solves
+        for (auto &sl : v->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.ev);
+            if (q == cudaErrorNotReady) {
+                running = true;
+                continue;
+            }
+            auto &r = v->reqs[sl.ticket];
+            r.t_done = std::chrono::steady_clock::now();
+            r.state = q == cudaSuccess ? 2 : 3;
+            r.status = q == cudaSuccess ? FSP_OK : FSP_ECUDA;
+            if (q != cudaSuccess) cudaGetLastError();
+            v->st.completed++;
+            v->idle_ws.push_back(sl.ws);
+            v->specs[sl.key].refs--;
+            sl.busy = false;
+            progress = true;
+        }
+        // admit queued requests into free slots, in arrival order
+        auto none_busy = [&]() {
+            for (auto &x : v->slots)
+                if (x.busy) return false;
+            return true;
+        };
+        // a request that cannot fit even with nothing running fails with ENOMEM
+        auto fail_front = [&](fsp_status why) {
+            auto &r = v->reqs[v->queue.front()];
+            r.state = 3, r.status = why, r.t_done = std::chrono::steady_clock::now();
+            v->queue.pop_front();
+            v->st.completed++;
+            progress = true;
+        };
+        while (!v->queue.empty()) {
+            int si = -1;
+            for (int i = 0; i < (int)v->slots.size(); ++i)
+                if (!v->slots[i].busy) {
+                    si = i;
+                    break;
+                }
+            if (si < 0) break;
+            const uint64_t t = v->queue.front();
+            auto &r = v->reqs[t];
+            auto key = std::make_tuple(r.N, bits_of(r.L), (int)r.algo, (int)r.dtype);
+            auto it = v->specs.find(key);
+            if (it == v->specs.end()) {
+                // spectrum-only plan; its size is known before it is built
+                const size_t P = ((r.N + 1) + 15) / 16 * 16;
+                const size_t rs = r.dtype == FSP_F64 ? 8 : 4;
+                const size_t need = (size_t)(r.N + 1) * (r.N + 1) * P * rs + 3 * (size_t)r.N * 2 * rs;
+                if (!server_make_room(v, need)) {  // wait for running solves to release memory
+                    if (none_busy()) {
+                        fail_front(FSP_ENOMEM);
+                        continue;
+                    }
+                    break;
+                }
+                fsp_plan *p = nullptr;
+                const fsp_status cs = plan_create_impl(&p, r.N, r.L, r.L / r.N, r.algo, r.dtype,
+                                                       reinterpret_cast<fsp_stream>(v->slots[si].stream), false);
+                if (cs != FSP_OK) {
+                    r.state = 3, r.status = cs, r.t_done = std::chrono::steady_clock::now();
+                    v->queue.pop_front();
+                    v->st.completed++;
+                    progress = true;
+                    continue;
+                }
+                fsp_server::Spec sp;
+                sp.plan = p, sp.bytes = p->bytes;
+                v->used += sp.bytes;
+                it = v->specs.emplace(key, sp).first;
+                v->st.spec_misses++;
+            } else {
+                v->st.spec_hits++;
+            }
+            it->second.refs++;  // pinned while a workspace is sought
+            fsp_server::WS ws;
+            bool have = false;
+            for (size_t i = 0; i < v->idle_ws.size(); ++i)
+                if (v->idle_ws[i].N == r.N && v->idle_ws[i].dtype == r.dtype) {
+                    ws = v->idle_ws[i];
+                    v->idle_ws.erase(v->idle_ws.begin() + i);
+                    have = true;
+                    break;
+                }
+            if (!have) {
+                const size_t wb = ws_bytes(r.N, r.dtype);
+                if (!server_make_room(v, wb)) {
+                    it->second.refs--;
+                    if (none_busy()) {
+                        fail_front(FSP_ENOMEM);
+                        continue;
+                    }
+                    break;
+                }
+                const size_t w1 = wb / 3;
+                if (cudaMalloc(&ws.W1, w1) != cudaSuccess || cudaMalloc(&ws.W2, 2 * w1) != cudaSuccess) {
+                    cudaGetLastError();
+                    if (ws.W1) cudaFree(ws.W1);
+                    ws.W1 = nullptr;
+                    it->second.refs--;
+                    if (none_busy()) {
+                        fail_front(FSP_ENOMEM);
+                        continue;
+                    }
+                    break;
+                }
+                ws.bytes = wb, ws.N = r.N, ws.dtype = r.dtype;
+                v->used += wb;
+            }
+            auto &sl = v->slots[si];
+            it->second.last_use = ++v->clock;
+            const cudaError_t e = enqueue_solve_ws(it->second.plan, r.rho, r.phi, ws.W1, ws.W2, sl.stream);
+            const cudaError_t e2 = e == cudaSuccess ? cudaEventRecord(sl.ev, sl.stream) : e;
+            v->queue.pop_front();
+            if (e2 != cudaSuccess) {
+                cudaGetLastError();
+                r.state = 3, r.status = FSP_ECUDA, r.t_done = std::chrono::steady_clock::now();
+                v->idle_ws.push_back(ws);
+                it->second.refs--;
+                v->st.completed++;
+            } else {
+                sl.busy = true, sl.ticket = t, sl.ws = ws, sl.key = key;
+                r.state = 1;
+                v->st.admitted++;
+                running = true;
+            }
+            progress = true;
+        }
+        if (progress) continue;
+        if (running) {
+            // a solve is on the device: poll its event closely (latency)
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        } else {
+            v->cv.wait_for(lk, std::chrono::milliseconds(2));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" fsp_status fsp_server_create(fsp_server **out, size_t hbm_budget_bytes, int max_slots) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    if (hbm_budget_bytes == 0 || max_slots < 1 || max_slots > 64) return FSP_EINVAL;
+    fsp_server *v = new fsp_server();
+    if (cudaGetDevice(&v->device) != cudaSuccess) {
+        delete v;
+        return FSP_ECUDA;
+    }
+    v->budget = hbm_budget_bytes, v->max_slots = max_slots, v->max_queue = 1 << 16;
+    v->slots.resize(max_slots);
+    for (auto &sl : v->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto &x : v->slots) {
+                if (x.stream) cudaStreamDestroy(x.stream);
+                if (x.ev) cudaEventDestroy(x.ev);
+            }
+            delete v;
+            return FSP_ECUDA;
+        }
+    }
+    v->magic = kServerMagic;
+    v->worker = std::thread(server_loop, v);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_servers.insert(v);
+    }
+    *out = v;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_server_submit(fsp_server *v, int N, double L, fsp_algo algo, fsp_dtype dtype,
+                                        const void *rho, void *phi, uint64_t *ticket) {
+    if (!server_live(v) || !ticket) return FSP_EINVAL;
+    fsp_status st = validate_size(N, L, algo);
+    if (st != FSP_OK) return st;
+    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED) return FSP_EINVAL;
+    if (!rho || !phi || !aligned16(rho) || !aligned16(phi)) return FSP_EINVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    if ((int)v->queue.size() >= v->max_queue) return FSP_EBUSY;
+    fsp_server::Req r;
+    r.N = N, r.L = L, r.algo = algo, r.dtype = dtype, r.rho = rho, r.phi = phi;
+    r.t_submit = std::chrono::steady_clock::now();
+    const uint64_t t = v->next_ticket++;
+    v->reqs.emplace(t, r);
+    v->queue.push_back(t);
+    v->st.submitted++;
+    *ticket = t;
+    v->cv.notify_one();
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_server_poll(fsp_server *v, uint64_t ticket, int *state, double *latency_ms) {
+    if (!server_live(v) || !state) return FSP_EINVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    auto it = v->reqs.find(ticket);
+    if (it == v->reqs.end()) return FSP_EINVAL;
+    *state = it->second.state;
+    if (it->second.state >= 2) {
+        if (latency_ms)
+            *latency_ms = std::chrono::duration<double, std::milli>(it->second.t_done - it->second.t_submit).count();
+        const fsp_status rs = it->second.status;
+        v->reqs.erase(it);  // a finished request is reported once
+        return rs;
+    }
+    if (latency_ms) *latency_ms = -1.0;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_server_get_stats(fsp_server *v, fsp_server_stats *out) {
+    if (!server_live(v) || !out) return FSP_EINVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    *out = v->st;
+    out->queued = v->queue.size();
+    out->running = 0;
+    for (auto &sl : v->slots) out->running += sl.busy ? 1 : 0;
+    out->bytes_in_use = v->used;
+    out->budget = v->budget;
+    out->cached_spectra = v->specs.size();
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_server_destroy(fsp_server *v) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!v || !g_servers.count(v)) return FSP_EINVAL;
+        g_servers.erase(v);
+    }
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stop = true;
+    }
+    v->cv.notify_all();
+    if (v->worker.joinable()) v->worker.join();
+    cudaSetDevice(v->device);
+    const cudaError_t e = cudaDeviceSynchronize();
+    for (auto &sl : v->slots) {
+        if (sl.busy) cudaFree(sl.ws.W1), cudaFree(sl.ws.W2);
+        cudaStreamDestroy(sl.stream);
+        cudaEventDestroy(sl.ev);
+    }
+    for (auto &w : v->idle_ws) cudaFree(w.W1), cudaFree(w.W2);
+    for (auto &kv : v->specs) fsp_plan_destroy(kv.second.plan);
+    v->magic = 0;
+    delete v;
+    return cuda_status(e);
+}

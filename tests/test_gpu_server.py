@@ -45,8 +45,11 @@ def test_same_result_alone_and_in_the_mix(fsp):
 
 
 def test_budget_is_respected_with_eviction(fsp):
-    # room for about one N=64 FP32 workspace plus two small spectra
-    budget = 3 * 64 * 64 * 80 * 8 + 3 * (65 * 65 * 80 * 4) + (1 << 20)
+    # room for one N=64 FP32 workspace (3*64*64*80 complex) and one N=64
+    # spectrum (65*65*80 reals + roots): a second spectrum forces an eviction
+    ws64 = 3 * 64 * 64 * 80 * 8
+    spec64 = 65 * 65 * 80 * 4 + 3 * 64 * 8
+    budget = ws64 + spec64 + 400_000
     srv = fsp.Server(budget_bytes=budget, max_slots=2)
     reqs = []
     for i, (N, L) in enumerate([(64, 1.0), (64, 2.0), (32, 1.0), (64, 1.0), (64, 2.0), (32, 2.0)]):

@@ -242,52 +242,79 @@ template <int R1, int R2, int R3> struct LastR {
 // Lines are columns (consecutive lines contiguous in memory): P2 (COL_FWD,
 // half-zero input, all n outputs), P4 (COL_INV, all inputs, first n/2
 // outputs), P3 (COL_FMI: forward with half-zero input, times S, inverse, first
-// n/2 outputs).  The last tile may be partial (nlines not a multiple of L).
+// n/2 outputs).  The last tile may be partial (N+1 lines, not a multiple of
+// L).  The workspace geometry is fixed by n = 2N (row pitch P = N+1 rounded up
+// to 16; W1 [z][y][kx], W2 [z][ky][kx], S [qz][qy][qx]), so every stride is a
+// compile-time constant and every address offset an immediate.
+__host__ __device__ constexpr int row_pitch(int N) { return ((N + 1) + 15) / 16 * 16; }
+
+template <int n, int MODE> struct ColGeo {
+    static constexpr int N = n / 2, P = row_pitch(N);
+    static constexpr long long NP = (long long)N * P;
+    static constexpr long long IN_POS = MODE == COL_FMI ? 2 * NP : P;
+    static constexpr long long IN_BATCH = MODE == COL_FWD ? NP : MODE == COL_FMI ? P : 2 * NP;
+    static constexpr long long OUT_POS = MODE == COL_FMI ? 2 * NP : P;
+    static constexpr long long OUT_BATCH = MODE == COL_FWD ? 2 * NP : MODE == COL_FMI ? P : NP;
+    static constexpr long long S_POS = (long long)(N + 1) * P, S_BATCH = P;
+};
+
 template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE>
 __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     using C = cx_t<T>;
-    constexpr int TPL = n / V;
+    using G = ColGeo<n, MODE>;
+    constexpr int TPL = n / V, N = G::N;
     constexpr int RL = LastR<R1, R2, R3>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int l = threadIdx.x % L, t = threadIdx.x / L;
     const int line = blockIdx.x * L + l;
-    const bool ok = line < a.nlines;
+    const bool ok = line <= N;
     const long long bt = blockIdx.y;
     const C *tw = reinterpret_cast<const C *>(a.tw);
-    const C *in = reinterpret_cast<const C *>(a.in) + bt * a.in_batch + line;
-    C *out = reinterpret_cast<C *>(a.out) + bt * a.out_batch + line;
+    // thread-relative bases: position p = t + c lives at base_t + c*POS
+    const C *in_t = reinterpret_cast<const C *>(a.in) + bt * G::IN_BATCH + line + (long long)t * G::IN_POS;
+    C *out_t = reinterpret_cast<C *>(a.out) + bt * G::OUT_BATCH + line + (long long)t * G::OUT_POS;
     C v[V];
 
     // stage 0 inputs straight from global memory
     constexpr bool HZ0 = MODE != COL_INV;
     constexpr int D0 = MODE == COL_INV ? +1 : -1;
-#pragma unroll
-    for (int k = 0; k < V / R1; ++k)
-#pragma unroll
-        for (int r = 0; r < (HZ0 ? R1 / 2 : R1); ++r) {
-            const int p = t + k * TPL + r * (n / R1);
-            v[k * R1 + r] = ok ? in[(long long)p * a.in_pos] : C{T(0), T(0)};
-        }
+    StaticFor<0, V / R1>::run([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        StaticFor<0, HZ0 ? R1 / 2 : R1>::run([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            constexpr long long c = k * TPL + r * (n / R1);
+            v[k * R1 + r] = ok ? in_t[c * G::IN_POS] : C{T(0), T(0)};
+        });
+    });
     Stg<T, D0, n, V, L>::template compute<R1, 1, HZ0, false>(v, t, tw);
     run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV>(v, buf, t, l, tw, false);
 
     if constexpr (MODE == COL_FMI) {
         // multiply by the real, even spectrum at the folded frequency
-        const T *S = reinterpret_cast<const T *>(a.S);
-        const int h2 = 2 * a.half;
-        const int fy = (int)bt <= a.half ? (int)bt : h2 - (int)bt;
-        const T *Sy = S + (long long)fy * a.s_batch + line;
-#pragma unroll
-        for (int k = 0; k < V / RL; ++k)
-#pragma unroll
-            for (int r = 0; r < RL; ++r) {
-                const int p = t + k * TPL + r * (n / RL);
-                const int fz = p <= a.half ? p : h2 - p;
-                const T s = ok ? Sy[(long long)fz * a.s_pos] : T(0);
+        // min(p, n - p); for most registers the branch is known at compile time
+        const int fy = (int)bt <= N ? (int)bt : n - (int)bt;
+        const T *Sy = reinterpret_cast<const T *>(a.S) + (long long)fy * G::S_BATCH + line;
+        const T *S_up = Sy + (long long)t * G::S_POS, *S_dn = Sy - (long long)t * G::S_POS;
+        StaticFor<0, V / RL>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            StaticFor<0, RL>::run([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr int c = k * TPL + r * (n / RL);
+                T s;
+                if constexpr (c + TPL - 1 <= N) {
+                    s = ok ? S_up[(long long)c * G::S_POS] : T(0);
+                } else if constexpr (c > N) {
+                    s = ok ? S_dn[(long long)(n - c) * G::S_POS] : T(0);
+                } else {
+                    const int p = t + c;
+                    const int fz = p <= N ? p : n - p;
+                    s = ok ? Sy[(long long)fz * G::S_POS] : T(0);
+                }
                 v[k * RL + r].x *= s;
                 v[k * RL + r].y *= s;
-            }
+            });
+        });
         // inverse, radix schedule reversed: its stage 0 is the forward's last
         // radix on the same butterflies, already in registers
         using SI = Stg<T, +1, n, V, L>;
@@ -299,22 +326,24 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
             run_rest<T, +1, n, V, L, R2, R1, 1, true>(v, buf, t, l, tw, true);
         }
         constexpr int RF = R1;  // last radix of the reversed schedule
-#pragma unroll
-        for (int k = 0; k < V / RF; ++k)
-#pragma unroll
-            for (int r = 0; r < RF / 2; ++r) {
-                const int p = t + k * TPL + r * (n / RF);
-                if (ok) out[(long long)p * a.out_pos] = v[k * RF + r];
-            }
+        StaticFor<0, V / RF>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            StaticFor<0, RF / 2>::run([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr long long c = k * TPL + r * (n / RF);
+                if (ok) out_t[c * G::OUT_POS] = v[k * RF + r];
+            });
+        });
     } else {
         constexpr bool HO = MODE == COL_INV;
-#pragma unroll
-        for (int k = 0; k < V / RL; ++k)
-#pragma unroll
-            for (int r = 0; r < (HO ? RL / 2 : RL); ++r) {
-                const int p = t + k * TPL + r * (n / RL);
-                if (ok) out[(long long)p * a.out_pos] = v[k * RL + r];
-            }
+        StaticFor<0, V / RL>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            StaticFor<0, HO ? RL / 2 : RL>::run([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr long long c = k * TPL + r * (n / RL);
+                if (ok) out_t[c * G::OUT_POS] = v[k * RL + r];
+            });
+        });
     }
 }
 
@@ -337,7 +366,7 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
     for (int idx = tid; idx < L * H; idx += NTH) {
         const int m = idx % H, rr = idx / H;
         C z = C{T(0), T(0)};
-        if (row0 + rr < a.nrows) z = reinterpret_cast<const C *>(x + (row0 + rr) * a.x_row)[m];
+        if (row0 + rr < a.nrows) z = reinterpret_cast<const C *>(x + (row0 + rr) * N)[m];
         buf[m * LD + rr] = z;
     }
     __syncthreads();
@@ -379,7 +408,7 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
     const int warp = tid >> 5, lane = tid & 31;
     for (int rr = warp; rr < L; rr += NTH / 32) {
         if (row0 + rr < a.nrows) {
-            C *crow = c + (row0 + rr) * a.c_row;
+            C *crow = c + (row0 + rr) * row_pitch(N);
             for (int k = lane; k <= N; k += 32) crow[k] = buf[k * LD + rr];
         }
     }
@@ -400,7 +429,7 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
     const int warp = tid >> 5, lane = tid & 31;
     for (int rr = warp; rr < L; rr += NTH / 32) {
         const bool okr = row0 + rr < a.nrows;
-        const C *crow = c + (row0 + rr) * a.c_row;
+        const C *crow = c + (row0 + rr) * row_pitch(N);
         for (int k = lane; k <= N; k += 32) buf[k * LD + rr] = okr ? crow[k] : C{T(0), T(0)};
     }
     __syncthreads();
@@ -432,7 +461,7 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
 #pragma unroll 4
     for (int idx = tid; idx < L * H; idx += NTH) {
         const int m = idx % H, rr = idx / H;
-        if (row0 + rr < a.nrows) reinterpret_cast<C *>(x + (row0 + rr) * a.x_row)[m] = buf[m * LD + rr];
+        if (row0 + rr < a.nrows) reinterpret_cast<C *>(x + (row0 + rr) * N)[m] = buf[m * LD + rr];
     }
 }
 

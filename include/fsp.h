@@ -59,8 +59,14 @@ typedef enum { FSP_HE = 0, FSP_VG = 1, FSP_VG_DCT = 2 } fsp_algo;
 /* FSP_F64: every step in double precision.
  * FSP_F32_MIXED: the solve (all transforms and the spectral multiply) in
  * single precision; the Green's spectrum is precomputed in double precision
- * and rounded once to single precision. */
-typedef enum { FSP_F64 = 0, FSP_F32_MIXED = 1 } fsp_dtype;
+ * and rounded once to single precision.
+ * FSP_F64_DF: double arrays in and out, FP64-class accuracy (about 1e-14
+ * relative), but the transforms run in double-float arithmetic (each value a
+ * pair of floats, hi + lo) on the FP32 pipes, which on this GPU are far faster
+ * than its FP64 pipes; the spectrum is the FP64 one split into float pairs.
+ * Only for N = 32, 64, 128, 256, 512 (FSP_EUNSUPPORTED otherwise); not in
+ * batches. */
+typedef enum { FSP_F64 = 0, FSP_F32_MIXED = 1, FSP_F64_DF = 2 } fsp_dtype;
 
 typedef struct fsp_plan fsp_plan;
 

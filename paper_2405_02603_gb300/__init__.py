@@ -19,7 +19,7 @@ FSP_OK, FSP_EINVAL, FSP_EUNSUPPORTED, FSP_ENOMEM, FSP_ECUDA, FSP_EBUSY, FSP_ETIM
 STATUS_NAMES = ["FSP_OK", "FSP_EINVAL", "FSP_EUNSUPPORTED", "FSP_ENOMEM", "FSP_ECUDA", "FSP_EBUSY",
                 "FSP_ETIMEOUT"]
 ALGOS = {"he": 0, "vg": 1, "vg_dct": 2}
-DTYPES = {"f64": 0, "f32": 1}
+DTYPES = {"f64": 0, "f32": 1, "f64df": 2}
 
 _lib = None
 
@@ -123,7 +123,7 @@ def _algo_code(algo):
 
 def torch_dtype(dtype):
     import torch
-    return torch.float64 if _dtype_code(dtype) == 0 else torch.float32
+    return torch.float32 if _dtype_code(dtype) == 1 else torch.float64
 
 
 class Plan:

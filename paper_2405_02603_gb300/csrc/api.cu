@@ -20,6 +20,7 @@
 
 #include "../../include/fsp.h"
 #include "batch.h"
+#include "df.cuh"
 #include "fast.h"
 #include "greens.h"
 #include "kernels.cuh"
@@ -364,6 +365,7 @@ cudaError_t enqueue_solve_generic(const fsp_plan *p, const void *rho, void *phi,
 
 // One solve of plan p with the given workspace (W1: N*N*P, W2: 2*N*N*P complex).
 cudaError_t enqueue_solve_ws(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
+    if (p->dtype == FSP_F64_DF) return enqueue_solve_fast<df>(p, rho, phi, W1, W2, s);
     if (p->fast)
         return p->dtype == FSP_F64 ? enqueue_solve_fast<double>(p, rho, phi, W1, W2, s)
                                    : enqueue_solve_fast<float>(p, rho, phi, W1, W2, s);
@@ -397,14 +399,15 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     *out = nullptr;
     fsp_status st = validate_size(N, L, algo);
     if (st != FSP_OK) return st;
-    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED) return FSP_EINVAL;
+    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED && dtype != FSP_F64_DF) return FSP_EINVAL;
     if (!(std::fabs(h - L / N) <= 1e-12 * std::fabs(L / N))) return FSP_EINVAL;
+    if (dtype == FSP_F64_DF && !fast::has<df>(N)) return FSP_EUNSUPPORTED;  // specialised kernels only
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();
 
     fsp_plan *p = new fsp_plan();
     p->N = N, p->L = L, p->h = L / N, p->algo = algo, p->dtype = dtype;
-    p->rsize = dtype == FSP_F64 ? 8 : 4;
+    p->rsize = dtype == FSP_F32_MIXED ? 4 : 8;  // caller's reals; a double-float is 8 bytes too
     p->P = ((N + 1) + 15) / 16 * 16;
     const size_t csize = 2 * p->rsize;
     // tiles: rows (length-N FFT, N+1 positions), columns (length 2N)
@@ -421,7 +424,8 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     {
         const char *g = std::getenv("FSP_GENERIC_ONLY");
         const bool generic_only = g && g[0] == '1';
-        p->fast = !generic_only && (dtype == FSP_F64 ? fast::has<double>(N) : fast::has<float>(N));
+        p->fast = dtype == FSP_F64_DF ||
+                  (!generic_only && (dtype == FSP_F64 ? fast::has<double>(N) : fast::has<float>(N)));
     }
     auto fail = [&](fsp_status e) {
         cudaStreamSynchronize(s);
@@ -444,6 +448,9 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     if (dtype == FSP_F64) {
         e = launch_roots<double>(p->tw_n, N, s);
         if (e == cudaSuccess) e = launch_roots<double>(p->tw_2n, 2 * N, s);
+    } else if (dtype == FSP_F64_DF) {
+        e = launch_roots<df>(p->tw_n, N, s);
+        if (e == cudaSuccess) e = launch_roots<df>(p->tw_2n, 2 * N, s);
     } else {
         e = launch_roots<float>(p->tw_n, N, s);
         if (e == cudaSuccess) e = launch_roots<float>(p->tw_2n, 2 * N, s);
@@ -458,8 +465,9 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
         if ((st = enqueue_dct_spectrum(N, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
         const double hh = p->h;
         const double scale = hh * hh * hh / ((2.0 * N) * (2.0 * N) * (2.0 * N));
-        e = dtype == FSP_F64 ? launch_store_S<double>((double *)Td.p, p->S, N, p->P, scale, s)
-                             : launch_store_S<float>((double *)Td.p, p->S, N, p->P, scale, s);
+        e = dtype == FSP_F64      ? launch_store_S<double>((double *)Td.p, p->S, N, p->P, scale, s)
+            : dtype == FSP_F64_DF ? launch_store_S<df>((double *)Td.p, p->S, N, p->P, scale, s)
+                                  : launch_store_S<float>((double *)Td.p, p->S, N, p->P, scale, s);
         if (e != cudaSuccess) return fail(FSP_ECUDA);
         if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FSP_ECUDA);
     }
@@ -559,8 +567,9 @@ fsp_status fsp_plan_spectrum(const fsp_plan *plan, double *s_host) {
     DevBuf d;
     fsp_status st = alloc_or_nomem(d, sizeof(double) * tot);
     if (st != FSP_OK) return st;
-    cudaError_t e = plan->dtype == FSP_F64 ? launch_load_S<double>(plan->S, (double *)d.p, plan->N, plan->P, 0)
-                                           : launch_load_S<float>(plan->S, (double *)d.p, plan->N, plan->P, 0);
+    cudaError_t e = plan->dtype == FSP_F64      ? launch_load_S<double>(plan->S, (double *)d.p, plan->N, plan->P, 0)
+                    : plan->dtype == FSP_F64_DF ? launch_load_S<df>(plan->S, (double *)d.p, plan->N, plan->P, 0)
+                                                : launch_load_S<float>(plan->S, (double *)d.p, plan->N, plan->P, 0);
     if (e != cudaSuccess) return FSP_ECUDA;
     return cuda_status(cudaMemcpy(s_host, d.p, sizeof(double) * tot, cudaMemcpyDeviceToHost));
 }
@@ -730,6 +739,7 @@ extern "C" fsp_status fsp_batch_create(fsp_batch **out, fsp_plan *const *plans, 
     for (int i = 0; i < count; ++i) {
         if (!plan_live(plans[i]) || !seen.insert(plans[i]).second) return FSP_EINVAL;  // distinct live plans
         if (plans[i]->dtype != plans[0]->dtype || plans[i]->device != plans[0]->device) return FSP_EINVAL;
+        if (plans[i]->dtype == FSP_F64_DF) return FSP_EUNSUPPORTED;  // batches use the generic engine
         if (!rho[i] || !phi[i] || !aligned16(rho[i]) || !aligned16(phi[i])) return FSP_EINVAL;
     }
     int dev = -1;
@@ -926,7 +936,7 @@ uint64_t bits_of(double x) {
 
 size_t ws_bytes(int N, fsp_dtype dtype) {
     const size_t P = ((N + 1) + 15) / 16 * 16;
-    return (size_t)N * N * P * (dtype == FSP_F64 ? 16 : 8) * 3;
+    return (size_t)N * N * P * (dtype == FSP_F32_MIXED ? 8 : 16) * 3;
 }
 
 // Free idle workspaces, then unreferenced spectra (least recently used first),
@@ -1006,7 +1016,7 @@ void server_loop(fsp_server *v) {
             if (it == v->specs.end()) {
                 // spectrum-only plan; its size is known before it is built
                 const size_t P = ((r.N + 1) + 15) / 16 * 16;
-                const size_t rs = r.dtype == FSP_F64 ? 8 : 4;
+                const size_t rs = r.dtype == FSP_F32_MIXED ? 4 : 8;
                 const size_t need = (size_t)(r.N + 1) * (r.N + 1) * P * rs + 3 * (size_t)r.N * 2 * rs;
                 if (!server_make_room(v, need)) {  // wait for running solves to release memory
                     if (none_busy()) {
@@ -1138,7 +1148,8 @@ extern "C" fsp_status fsp_server_submit(fsp_server *v, int N, double L, fsp_algo
     if (!server_live(v) || !ticket) return FSP_EINVAL;
     fsp_status st = validate_size(N, L, algo);
     if (st != FSP_OK) return st;
-    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED) return FSP_EINVAL;
+    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED && dtype != FSP_F64_DF) return FSP_EINVAL;
+    if (dtype == FSP_F64_DF && !fast::has<df>(N)) return FSP_EUNSUPPORTED;
     if (!rho || !phi || !aligned16(rho) || !aligned16(phi)) return FSP_EINVAL;
     std::lock_guard<std::mutex> lk(v->mu);
     if ((int)v->queue.size() >= v->max_queue) return FSP_EBUSY;

@@ -19,8 +19,10 @@
 // twiddles w_n^(r (b mod Ns) n/(Ns R)), outputs at (b - b mod Ns) R +
 // b mod Ns + r Ns -- the self-sorting Stockham form of the generic engine.
 #pragma once
+#include <type_traits>
 #include <utility>
 
+#include "df.cuh"
 #include "fast.h"
 #include "kernels.cuh"
 
@@ -45,6 +47,29 @@ __host__ __device__ constexpr double cos32(int m) {
     return m <= 8 ? c32_base(m) : m <= 16 ? -c32_base(16 - m) : m <= 24 ? -c32_base(m - 16) : c32_base(32 - m);
 }
 __host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+// Type of the caller's real arrays (rho, phi): the compute type itself, except
+// for double-float, whose solves read and write double.
+template <typename T> struct io_of {
+    using t = T;
+};
+template <> struct io_of<df> {
+    using t = double;
+};
+template <typename T> __device__ __forceinline__ cx_t<T> load_pair(const typename io_of<T>::t *row, int m) {
+    if constexpr (std::is_same<T, df>::value) {
+        const double2 q = reinterpret_cast<const double2 *>(row)[m];
+        return cdf{df_from_double(q.x), df_from_double(q.y)};
+    } else {
+        return reinterpret_cast<const cx_t<T> *>(row)[m];
+    }
+}
+template <typename T> __device__ __forceinline__ void store_pair(typename io_of<T>::t *row, int m, cx_t<T> v) {
+    if constexpr (std::is_same<T, df>::value)
+        reinterpret_cast<double2 *>(row)[m] = double2{df_to_double(v.x), df_to_double(v.y)};
+    else
+        reinterpret_cast<cx_t<T> *>(row)[m] = v;
+}
 
 template <int I, int E> struct StaticFor {
     template <class F> static __device__ __forceinline__ void run(F &&f) {
@@ -75,7 +100,7 @@ template <typename T, int D> struct RD {
             return D < 0 ? cmuli(a) : cmulmi(a);
         } else {
             constexpr T c = T(cos32(m)), s = T(D * sin32(m));
-            return C{c * a.x - s * a.y, s * a.x + c * a.y};
+            return cmul(a, C{c, s});
         }
     }
 
@@ -169,7 +194,7 @@ template <typename T, int D, int n, int V, int L> struct Stg {
 
     // exp(D 2 pi i e / n) from the forward roots table
     static __device__ __forceinline__ C twid(const C *__restrict__ tw, int e) {
-        C w = __ldg(tw + e);
+        C w = ldg_c(tw + e);
         if (D > 0) w.y = -w.y;
         return w;
     }
@@ -360,13 +385,14 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int tid = threadIdx.x, l = tid % L, t = tid / L;
     const long long row0 = (long long)blockIdx.x * L;
-    const T *x = reinterpret_cast<const T *>(a.x);
+    using R = typename io_of<T>::t;
+    const R *x = reinterpret_cast<const R *>(a.x);
     // coalesced row loads of the packed pairs (x[2m], x[2m+1]), m < N/2
 #pragma unroll 4
     for (int idx = tid; idx < L * H; idx += NTH) {
         const int m = idx % H, rr = idx / H;
         C z = C{T(0), T(0)};
-        if (row0 + rr < a.nrows) z = reinterpret_cast<const C *>(x + (row0 + rr) * N)[m];
+        if (row0 + rr < a.nrows) z = load_pair<T>(x + (row0 + rr) * N, m);
         buf[m * LD + rr] = z;
     }
     __syncthreads();
@@ -393,7 +419,7 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
         const C zk = buf[k * LD + l], zc = buf[kc * LD + l];
         const C e = C{T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
         const C o = C{T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
-        const C wo = cmul(__ldg(tw2 + k), o);
+        const C wo = cmul(ldg_c(tw2 + k), o);
         if (k == 0) {
             buf[l] = cadd(e, o);
             buf[N * LD + l] = csub(e, o);
@@ -440,7 +466,7 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
         const C xk = buf[k * LD + l], xc = buf[kc * LD + l];
         const C A = C{xk.x + xc.x, xk.y - xc.y};
         const C B = C{xk.x - xc.x, xk.y + xc.y};
-        const C w = __ldg(tw2 + k);
+        const C w = ldg_c(tw2 + k);
         buf[k * LD + l] = cadd(A, cmuli(cmul(cconj(w), B)));
         if (k != 0 && 2 * k != N) buf[kc * LD + l] = cadd(cconj(A), cmuli(cmul(w, cconj(B))));
     }
@@ -457,11 +483,12 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
 #pragma unroll
         for (int r = 0; r < RL / 2; ++r) buf[(t + k * TPL + r * (N / RL)) * LD + l] = v[k * RL + r];
     __syncthreads();
-    T *x = reinterpret_cast<T *>(const_cast<void *>(a.x));
+    using R = typename io_of<T>::t;
+    R *x = reinterpret_cast<R *>(const_cast<void *>(a.x));
 #pragma unroll 4
     for (int idx = tid; idx < L * H; idx += NTH) {
         const int m = idx % H, rr = idx / H;
-        if (row0 + rr < a.nrows) reinterpret_cast<C *>(x + (row0 + rr) * N)[m] = buf[m * LD + rr];
+        if (row0 + rr < a.nrows) store_pair<T>(x + (row0 + rr) * N, m, buf[m * LD + rr]);
     }
 }
 
@@ -488,6 +515,12 @@ FSP_CFG(double, 128, 16, 8, 8, 16, 1)
 FSP_CFG(double, 256, 16, 8, 16, 16, 1)
 FSP_CFG(double, 512, 8, 8, 8, 8, 8)
 FSP_CFG(double, 1024, 16, 8, 16, 8, 8)
+FSP_CFG(df, 32, 8, 16, 4, 8, 1)
+FSP_CFG(df, 64, 8, 16, 8, 8, 1)
+FSP_CFG(df, 128, 16, 8, 8, 16, 1)
+FSP_CFG(df, 256, 16, 8, 16, 16, 1)
+FSP_CFG(df, 512, 8, 8, 8, 8, 8)
+FSP_CFG(df, 1024, 16, 8, 16, 8, 8)
 #undef FSP_CFG
 
 template <typename T, int n> constexpr size_t smem_for(int positions) {

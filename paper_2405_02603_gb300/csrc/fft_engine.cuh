@@ -30,6 +30,8 @@ template <typename T> using cx_t = typename cx<T>::t;
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+
+template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }

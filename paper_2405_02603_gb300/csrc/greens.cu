@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "greens.h"
 
 namespace fsp {
@@ -139,6 +140,8 @@ template <typename T> cudaError_t launch_load_S(const void *S, double *Sd, int N
 }
 
 template cudaError_t launch_store_S<float>(const double *, void *, int, int, double, cudaStream_t);
+template cudaError_t launch_store_S<df>(const double *, void *, int, int, double, cudaStream_t);
+template cudaError_t launch_load_S<df>(const void *, double *, int, int, cudaStream_t);
 template cudaError_t launch_store_S<double>(const double *, void *, int, int, double, cudaStream_t);
 template cudaError_t launch_load_S<float>(const void *, double *, int, int, cudaStream_t);
 template cudaError_t launch_load_S<double>(const void *, double *, int, int, cudaStream_t);

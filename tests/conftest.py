@@ -31,7 +31,7 @@ def fsp():
 def to_dev(a, dtype="f64"):
     import numpy as np
     import torch
-    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64 if dtype == "f64" else np.float32))
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32 if dtype == "f32" else np.float64))
     return t.cuda()
 
 

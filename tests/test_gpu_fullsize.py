@@ -18,7 +18,7 @@ from conftest import e_max, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 2e-6}
+TOL = {"f64": 1e-12, "f32": 2e-6, "f64df": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +29,7 @@ def ref256(orc):
     return N, L, rho, orc.solve_fft(T, rho, L / N)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f64df"])
 @pytest.mark.parametrize("algo", ["vg", "vg_dct"])
 def test_n256_full_field(fsp, ref256, algo, dtype):
     N, L, rho, ref = ref256
@@ -41,7 +41,7 @@ def test_n256_full_field(fsp, ref256, algo, dtype):
     p.close()
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f64df"])
 def test_n512_he_sampled_direct_sum(fsp, orc, dtype):
     N, L = 512, 1.0
     h = L / N

@@ -271,7 +271,8 @@ def batch_leg(fsp, dtype, count=64, launches=5):
             "ms_per_launch": round(ms, 3), "value": round(count / (ms * 1e-3), 1), "unit": "solves/s",
             "hbm_gbs": round(bytes_alg / (ms * 1e-3) / 1e9, 1), "launches": launches,
             "status": "FSP_OK" if status == 0 else "status %d" % status,
-            "form": "one persistent kernel per launch over all 64 solves, CUDA graph replay"}
+            "form": "one persistent kernel per launch over all 64 solves, CUDA graph replay",
+            "tiles": "generic-engine tile shapes from the autotuned table paper_2405_02603_gb300/tuning/gb300.txt"}
 
 
 SERVE_SIZES = [32, 64, 96, 128, 192, 256]

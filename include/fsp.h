@@ -213,6 +213,12 @@ fsp_status fsp_batch_set_timeout(fsp_batch *batch, double ms);
  * its time limit.  Later launches then end with FSP_ETIMEOUT. */
 fsp_status fsp_batch_inject_stall(fsp_batch *batch);
 fsp_status fsp_batch_destroy(fsp_batch *batch);
+/* Tune this batch's tile shapes in place: coordinate descent over the
+ * generic engine's row and column shapes of each distinct N (largest first),
+ * timing graph replays of the batch itself; the winners are kept by the batch
+ * and recorded in the tuning table (fsp_tuning_get).  Launches the batch many
+ * times (it reads rho, overwrites phi); synchronises `stream`. */
+fsp_status fsp_batch_autotune(fsp_batch *batch, fsp_stream stream);
 /* create + launch + wait + destroy in one call. */
 fsp_status fsp_solve_batched(fsp_plan *const *plans, const void *const *rho, void *const *phi, int count,
                              fsp_stream stream);
@@ -254,6 +260,24 @@ fsp_status fsp_server_poll(fsp_server *server, uint64_t ticket, int *state, doub
 fsp_status fsp_server_get_stats(fsp_server *server, fsp_server_stats *out);
 /* Stops the worker, waits for the device, frees everything. */
 fsp_status fsp_server_destroy(fsp_server *server);
+
+/* ------------------------------------------------------------ autotune --
+ * Tile shapes of the generic mixed-radix engine (the lines per CTA of its row
+ * and column passes; used by every solve of a non-power-of-two N and by all
+ * batched solves).  The shape changes no result bit (each line's arithmetic is
+ * the same), only speed.
+ *
+ * fsp_autotune times every feasible shape for (N, dtype) on the current device
+ * (builds a temporary plan, a few ms of solves per shape; synchronises
+ * `stream`), records the fastest in a process-wide table and returns it.
+ * dtype: FSP_F64 or FSP_F32_MIXED.  Plans created later for (N, dtype) use the
+ * table's shape.
+ * fsp_tuning_get writes the table as text, one "N dtype lgL_row lgL_col" line
+ * per entry (NUL-terminated); *len receives the size needed (buf may be NULL).
+ * fsp_tuning_set merges such text into the table (pins a tuned table). */
+fsp_status fsp_autotune(int N, fsp_dtype dtype, fsp_stream stream, int *lgL_row, int *lgL_col);
+fsp_status fsp_tuning_get(char *buf, size_t cap, size_t *len);
+fsp_status fsp_tuning_set(const char *text);
 
 /*
  * fsp_solve_noalloc -- an FP64 solve that allocates no device memory.  The

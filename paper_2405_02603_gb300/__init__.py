@@ -82,12 +82,19 @@ def lib(build_if_missing=True):
     L.fsp_batch_inject_stall.argtypes = [vp]
     L.fsp_batch_destroy.argtypes = [vp]
     L.fsp_solve_batched.argtypes = [vpp, vpp, vpp, i, vp]
+    L.fsp_batch_autotune.argtypes = [vp, vp]
+    L.fsp_batch_autotune.restype = i
     u64 = ctypes.c_uint64
     L.fsp_server_create.argtypes = [vpp, ctypes.c_size_t, i]
     L.fsp_server_submit.argtypes = [vp, i, d, i, i, vp, vp, ctypes.POINTER(u64)]
     L.fsp_server_poll.argtypes = [vp, u64, ctypes.POINTER(i), ctypes.POINTER(d)]
     L.fsp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     L.fsp_server_destroy.argtypes = [vp]
+    L.fsp_autotune.argtypes = [i, i, vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.fsp_tuning_get.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.fsp_tuning_set.argtypes = [ctypes.c_char_p]
+    for name in ("fsp_autotune", "fsp_tuning_get", "fsp_tuning_set"):
+        getattr(L, name).restype = i
     for name in ("fsp_server_create", "fsp_server_submit", "fsp_server_poll", "fsp_server_get_stats",
                  "fsp_server_destroy"):
         getattr(L, name).restype = i
@@ -98,6 +105,9 @@ def lib(build_if_missing=True):
                  "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc"):
         getattr(L, name).restype = i
     _lib = L
+    table = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.txt")
+    if os.path.exists(table):  # pinned tile shapes measured on a GB300
+        check(L.fsp_tuning_set(open(table, "rb").read()), "fsp_tuning_set")
     return L
 
 
@@ -222,6 +232,29 @@ def kernel_T(N, L=1.0, algo="vg_dct", stream=None):
     return t
 
 
+def autotune(N, dtype="f32", stream=None):
+    """Time the generic engine's tile shapes for (N, dtype); returns (lgL_row,
+    lgL_col) and records them for plans created afterwards."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(lib().fsp_autotune(int(N), _dtype_code(dtype), _stream_handle(stream), ctypes.byref(a), ctypes.byref(b)),
+          "fsp_autotune")
+    return a.value, b.value
+
+
+def tuning_get():
+    """The tuning table as text ("N dtype lgL_row lgL_col" per line)."""
+    n = ctypes.c_size_t()
+    check(lib().fsp_tuning_get(None, 0, ctypes.byref(n)), "fsp_tuning_get")
+    buf = ctypes.create_string_buffer(n.value)
+    check(lib().fsp_tuning_get(buf, n.value, ctypes.byref(n)), "fsp_tuning_get")
+    return buf.value.decode()
+
+
+def tuning_set(text):
+    """Merge table text into the tuning table (pins tile shapes)."""
+    check(lib().fsp_tuning_set(text.encode() if isinstance(text, str) else text), "fsp_tuning_set")
+
+
 def _ptr_array(xs):
     return (ctypes.c_void_p * len(xs))(*[ctypes.c_void_p(x) for x in xs])
 
@@ -251,6 +284,10 @@ class Batch:
 
     def set_timeout(self, ms):
         check(lib().fsp_batch_set_timeout(self._b, float(ms)), "fsp_batch_set_timeout")
+
+    def autotune(self, stream=None):
+        """Tune the batch's tile shapes by timing its own launches."""
+        check(lib().fsp_batch_autotune(self._b, _stream_handle(stream)), "fsp_batch_autotune")
 
     def inject_stall(self):
         check(lib().fsp_batch_inject_stall(self._b), "fsp_batch_inject_stall")
@@ -378,4 +415,4 @@ def fft_c2c(x, sign=-1, stream=None):
     return out
 
 
-__all__ = ["Plan", "Batch", "Server", "solve_batched", "FspError", "kernel_T", "fft_c2c", "solve_noalloc", "lib", "check", "library_path", "ALGOS", "DTYPES"]
+__all__ = ["autotune", "tuning_get", "tuning_set", "Plan", "Batch", "Server", "solve_batched", "FspError", "kernel_T", "fft_c2c", "solve_noalloc", "lib", "check", "library_path", "ALGOS", "DTYPES"]

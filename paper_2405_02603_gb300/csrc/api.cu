@@ -9,7 +9,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -89,6 +91,19 @@ struct TileCfg {
     Stages st;
     int tpl = 0, lgL = 0;
 };
+
+// Tile shapes (log2 lines per CTA) of the generic engine chosen by the
+// autotuner or loaded from a table, per (N, dtype): {rows, columns}.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, std::pair<int, int>> g_tuning;
+
+bool tuned_lgL(int N, int dtype, int &row, int &col) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuning.find({N, dtype});
+    if (it == g_tuning.end()) return false;
+    row = it->second.first, col = it->second.second;
+    return true;
+}
 
 bool make_cfg(int n, int positions, size_t csize, int want_lgL, TileCfg &c) {
     if (!make_stages(n, c.st)) return false;
@@ -411,7 +426,8 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     p->P = ((N + 1) + 15) / 16 * 16;
     const size_t csize = 2 * p->rsize;
     // tiles: rows (length-N FFT, N+1 positions), columns (length 2N)
-    const int row_lgL = dtype == FSP_F64 ? 3 : 4, col_lgL = dtype == FSP_F64 ? 3 : 4;
+    int row_lgL = dtype == FSP_F32_MIXED ? 4 : 3, col_lgL = dtype == FSP_F32_MIXED ? 4 : 3;
+    tuned_lgL(N, (int)dtype, row_lgL, col_lgL);
     if (!make_cfg(N, N + 1, csize, row_lgL, p->row) || !make_cfg(2 * N, 2 * N, csize, col_lgL, p->col)) {
         delete p;
         return FSP_EUNSUPPORTED;
@@ -639,6 +655,10 @@ struct fsp_batch {
     uint64_t magic = 0;
     int device = 0, count = 0;
     fsp_dtype dtype = FSP_F64;
+    std::vector<fsp_plan *> plans;
+    std::vector<const void *> rho;
+    std::vector<void *> phi;
+    std::map<int, std::pair<int, int>> shape;  // per N: (lgL_row, lgL_col) of its tiles
     std::vector<BatchSolve> solves;
     std::vector<BatchSeg> segs;
     int total = 0;
@@ -673,18 +693,18 @@ void batch_free(fsp_batch *b) {
 
 // Fill the device-side descriptor of one solve from its plan (generic engine
 // tile shapes; workspace reads through L2).
-BatchSolve batch_solve_of(const fsp_plan *p, const void *rho, void *phi) {
+BatchSolve batch_solve_of(const fsp_plan *p, const void *rho, void *phi, const TileCfg &row, const TileCfg &col) {
     const int N = p->N;
     const long long P = p->P;
     BatchSolve b{};
     RowsArgs r{};
     r.c = p->W1, r.x_row = N, r.c_row = P, r.N = N, r.nrows = N * N;
-    r.lgL = p->row.lgL, r.tpl = p->row.tpl, r.st = p->row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    r.lgL = row.lgL, r.tpl = row.tpl, r.st = row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
     b.r1 = r, b.r5 = r;
     b.r1.x = rho;
     b.r5.x = phi;
     LinesArgs a{};
-    a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_2n;
+    a.st = col.st, a.tpl = col.tpl, a.lgL = col.lgL, a.tw = p->tw_2n;
     a.nlines = N + 1;
     LinesArgs c2 = a;
     c2.in = p->W1, c2.out = p->W2;
@@ -702,8 +722,8 @@ BatchSolve batch_solve_of(const fsp_plan *p, const void *rho, void *phi) {
     c4.out_pos = P, c4.out_line = 1, c4.out_batch = (long long)N * P;
     c4.n_in = 2 * N, c4.n_out = N, c4.nbatch = N;
     b.c2 = c2, b.c3 = c3, b.c4 = c4;
-    b.ntx = (N + 1 + (1 << p->col.lgL) - 1) >> p->col.lgL;
-    const int ntr = (N * N + (1 << p->row.lgL) - 1) >> p->row.lgL;
+    b.ntx = (N + 1 + (1 << col.lgL) - 1) >> col.lgL;
+    const int ntr = (N * N + (1 << row.lgL) - 1) >> row.lgL;
     b.ntiles[0] = ntr, b.ntiles[1] = b.ntx * N, b.ntiles[2] = b.ntx * 2 * N, b.ntiles[3] = b.ntx * N, b.ntiles[4] = ntr;
     return b;
 }
@@ -730,6 +750,79 @@ fsp_status batch_build_graph(fsp_batch *b) {
 
 }  // namespace
 
+namespace {
+
+// Tile shapes a batch uses for one of its plans: the per-N override if set,
+// else the plan's own generic-engine shapes.
+void batch_tiles(const fsp_batch *b, const fsp_plan *p, TileCfg &row, TileCfg &col) {
+    row = p->row, col = p->col;
+    auto it = b->shape.find(p->N);
+    if (it == b->shape.end()) return;
+    const size_t csize = 2 * p->rsize;
+    TileCfg r = row, c = col;
+    if (choose_tile(p->N + 1, r.tpl, csize, it->second.first, r.lgL)) row = r;
+    if (choose_tile(2 * p->N, c.tpl, csize, it->second.second, c.lgL)) col = c;
+}
+
+// (Re)build descriptors, work list, device arrays and graph of a batch.
+fsp_status batch_build(fsp_batch *b, cudaStream_t s) {
+    const int count = b->count;
+    const size_t csize = 2 * b->plans[0]->rsize;
+    b->solves.clear();
+    b->segs.clear();
+    int threads = 32;
+    size_t smem = 0;
+    for (int i = 0; i < count; ++i) {
+        const fsp_plan *p = b->plans[i];
+        TileCfg row, col;
+        batch_tiles(b, p, row, col);
+        b->solves.push_back(batch_solve_of(p, b->rho[i], b->phi[i], row, col));
+        threads = std::max(threads, std::max((1 << row.lgL) * row.tpl, (1 << col.lgL) * col.tpl));
+        smem = std::max(smem, std::max((size_t)(p->N + 1) * ((1 << row.lgL) + 1) * csize,
+                                       (size_t)(2 * p->N) * ((1 << col.lgL) + 1) * csize));
+    }
+    threads = (threads + 31) / 32 * 32;
+    // pass-major work list; within a pass, larger solves first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->plans[x]->N > b->plans[y]->N; });
+    int first = 0;
+    for (int pass = 0; pass < 5; ++pass)
+        for (int i : order) {
+            BatchSeg g{};
+            g.solve = i, g.pass = pass, g.first = first, g.ntiles = b->solves[i].ntiles[pass];
+            g.need_prev = pass ? b->solves[i].ntiles[pass - 1] : 0;
+            first += g.ntiles;
+            b->segs.push_back(g);
+        }
+    b->total = first;
+    for (void *q : {(void *)b->d_solves, (void *)b->d_segs, (void *)b->d_ctl})
+        if (q) cudaFree(q);
+    b->d_solves = nullptr, b->d_segs = nullptr, b->d_ctl = nullptr;
+    b->ctl_bytes = sizeof(BatchCtl) + sizeof(int) * (5 * (size_t)count);
+    DevBuf ds, dg, dc;
+    fsp_status st;
+    if ((st = alloc_or_nomem(ds, sizeof(BatchSolve) * count)) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(dg, sizeof(BatchSeg) * b->segs.size())) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(dc, b->ctl_bytes)) != FSP_OK) return st;
+    b->d_solves = (BatchSolve *)ds.release(), b->d_segs = (BatchSeg *)dg.release(), b->d_ctl = (BatchCtl *)dc.release();
+    if (cudaMemcpyAsync(b->d_solves, b->solves.data(), sizeof(BatchSolve) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_segs, b->segs.data(), sizeof(BatchSeg) * b->segs.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FSP_ECUDA;
+    const int per_sm = b->dtype == FSP_F64 ? batch_blocks_per_sm<double>(threads, smem) : batch_blocks_per_sm<float>(threads, smem);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (per_sm < 1 || sms < 1) return FSP_EUNSUPPORTED;
+    b->launch.solves = b->d_solves, b->launch.segs = b->d_segs, b->launch.nseg = (int)b->segs.size();
+    b->launch.total = b->total, b->launch.ctl = b->d_ctl;
+    b->launch.grid = (unsigned)std::min<long long>((long long)sms * per_sm, b->total);
+    b->launch.threads = threads, b->launch.smem = smem;
+    return batch_build_graph(b);
+}
+
+}  // namespace
+
 extern "C" fsp_status fsp_batch_create(fsp_batch **out, fsp_plan *const *plans, const void *const *rho,
                                        void *const *phi, int count, fsp_stream stream) {
     if (!out) return FSP_EINVAL;
@@ -747,56 +840,14 @@ extern "C" fsp_status fsp_batch_create(fsp_batch **out, fsp_plan *const *plans, 
     if (dev != plans[0]->device) return FSP_EINVAL;
     fsp_batch *b = new fsp_batch();
     b->device = dev, b->count = count, b->dtype = plans[0]->dtype;
-    const size_t csize = 2 * plans[0]->rsize;
-    int threads = 32;
-    size_t smem = 0;
-    for (int i = 0; i < count; ++i) {
-        const fsp_plan *p = plans[i];
-        b->solves.push_back(batch_solve_of(p, rho[i], phi[i]));
-        threads = std::max(threads, std::max((1 << p->row.lgL) * p->row.tpl, (1 << p->col.lgL) * p->col.tpl));
-        smem = std::max(smem, std::max((size_t)(p->N + 1) * ((1 << p->row.lgL) + 1) * csize,
-                                       (size_t)(2 * p->N) * ((1 << p->col.lgL) + 1) * csize));
-    }
-    threads = (threads + 31) / 32 * 32;
-    // pass-major work list; within a pass, larger solves first
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return plans[x]->N > plans[y]->N; });
-    int first = 0;
-    for (int pass = 0; pass < 5; ++pass)
-        for (int i : order) {
-            BatchSeg g{};
-            g.solve = i, g.pass = pass, g.first = first, g.ntiles = b->solves[i].ntiles[pass];
-            g.need_prev = pass ? b->solves[i].ntiles[pass - 1] : 0;
-            first += g.ntiles;
-            b->segs.push_back(g);
-        }
-    b->total = first;
-    auto fail = [&](fsp_status st) {
+    b->plans.assign(plans, plans + count);
+    b->rho.assign(rho, rho + count);
+    b->phi.assign(phi, phi + count);
+    const fsp_status st = batch_build(b, reinterpret_cast<cudaStream_t>(stream));
+    if (st != FSP_OK) {
         batch_free(b);
         return st;
-    };
-    b->ctl_bytes = sizeof(BatchCtl) + sizeof(int) * (5 * (size_t)count);
-    DevBuf ds, dg, dc;
-    fsp_status st;
-    if ((st = alloc_or_nomem(ds, sizeof(BatchSolve) * count)) != FSP_OK) return fail(st);
-    if ((st = alloc_or_nomem(dg, sizeof(BatchSeg) * b->segs.size())) != FSP_OK) return fail(st);
-    if ((st = alloc_or_nomem(dc, b->ctl_bytes)) != FSP_OK) return fail(st);
-    b->d_solves = (BatchSolve *)ds.release(), b->d_segs = (BatchSeg *)dg.release(), b->d_ctl = (BatchCtl *)dc.release();
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(b->d_solves, b->solves.data(), sizeof(BatchSolve) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_segs, b->segs.data(), sizeof(BatchSeg) * b->segs.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return fail(FSP_ECUDA);
-    const int per_sm = b->dtype == FSP_F64 ? batch_blocks_per_sm<double>(threads, smem) : batch_blocks_per_sm<float>(threads, smem);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (per_sm < 1 || sms < 1) return fail(FSP_EUNSUPPORTED);
-    b->launch.solves = b->d_solves, b->launch.segs = b->d_segs, b->launch.nseg = (int)b->segs.size();
-    b->launch.total = b->total, b->launch.ctl = b->d_ctl;
-    b->launch.grid = (unsigned)std::min<long long>((long long)sms * per_sm, b->total);
-    b->launch.threads = threads, b->launch.smem = smem;
-    if ((st = batch_build_graph(b)) != FSP_OK) return fail(st);
+    }
     b->magic = kBatchMagic;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -835,6 +886,67 @@ extern "C" fsp_status fsp_batch_inject_stall(fsp_batch *b) {
         }
     if (cudaMemcpy(b->d_segs, b->segs.data(), sizeof(BatchSeg) * b->segs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return FSP_ECUDA;
+    return FSP_OK;
+}
+
+namespace {
+// Best of `reps` launches of the batch's graph, in ms; negative on error.
+double time_batch(fsp_batch *b, cudaStream_t s, int reps) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    cudaError_t e = cudaGraphLaunch(b->exec, s);  // warm-up
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) {
+        cudaEventRecord(e0, s);
+        e = cudaGraphLaunch(b->exec, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) e = cudaErrorUnknown;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int status = 0;
+    cudaMemcpy(&status, &b->d_ctl->status, sizeof(int), cudaMemcpyDeviceToHost);
+    return (e == cudaSuccess && status == 0) ? best : -1.0;
+}
+}  // namespace
+
+extern "C" fsp_status fsp_batch_autotune(fsp_batch *b, fsp_stream stream) {
+    if (!batch_live(b)) return FSP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int> Ns;
+    for (auto *p : b->plans)
+        if (std::find(Ns.begin(), Ns.end(), p->N) == Ns.end()) Ns.push_back(p->N);
+    std::sort(Ns.begin(), Ns.end(), std::greater<int>());
+    for (int N : Ns)
+        for (auto *p : b->plans)
+            if (p->N == N && !b->shape.count(N)) b->shape[N] = {p->row.lgL, p->col.lgL};
+    fsp_status st = batch_build(b, s);
+    if (st != FSP_OK) return st;
+    double best = time_batch(b, s, 3);
+    if (best < 0) return FSP_ECUDA;
+    // coordinate descent, largest N first: columns, then rows
+    for (int N : Ns)
+        for (int which = 1; which >= 0; --which)
+            for (int lg = 0; lg <= 5; ++lg) {
+                auto keep = b->shape[N];
+                auto trial = keep;
+                (which ? trial.second : trial.first) = lg;
+                if (trial == keep) continue;
+                b->shape[N] = trial;
+                if ((st = batch_build(b, s)) != FSP_OK) return st;
+                const double t = time_batch(b, s, 3);
+                if (t > 0 && t < best)
+                    best = t;
+                else
+                    b->shape[N] = keep;
+            }
+    if ((st = batch_build(b, s)) != FSP_OK) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : b->shape) g_tuning[{kv.first, (int)b->dtype}] = kv.second;
     return FSP_OK;
 }
 
@@ -1219,4 +1331,116 @@ extern "C" fsp_status fsp_server_destroy(fsp_server *v) {
     v->magic = 0;
     delete v;
     return cuda_status(e);
+}
+
+// ------------------------------------------------------------ autotune --
+namespace {
+
+// Time `reps` generic-engine solves of plan p with tile shapes (lr, lc); the
+// best of three rounds, in ms per solve, or a negative value when the shape
+// does not fit (threads or shared memory).
+double time_generic(fsp_plan *p, int lr, int lc, const void *rho, void *phi, cudaStream_t s, int reps) {
+    const size_t csize = 2 * p->rsize;
+    TileCfg row = p->row, col = p->col;
+    if (!choose_tile(p->N + 1, row.tpl, csize, lr, row.lgL) || row.lgL != lr) return -1.0;
+    if (!choose_tile(2 * p->N, col.tpl, csize, lc, col.lgL) || col.lgL != lc) return -1.0;
+    const TileCfg save_r = p->row, save_c = p->col;
+    p->row = row, p->col = col;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    double best = 1e30;
+    cudaError_t e = cudaSuccess;
+    for (int round = 0; round < 4 && e == cudaSuccess; ++round) {
+        cudaEventRecord(a, s);
+        for (int i = 0; i < reps && e == cudaSuccess; ++i)
+            e = p->dtype == FSP_F64 ? enqueue_solve_generic<double>(p, rho, phi, p->W1, p->W2, s)
+                                    : enqueue_solve_generic<float>(p, rho, phi, p->W1, p->W2, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (round > 0) best = std::min(best, (double)ms / reps);  // round 0 warms up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    p->row = save_r, p->col = save_c;
+    return e == cudaSuccess ? best : -2.0;
+}
+
+}  // namespace
+
+extern "C" fsp_status fsp_autotune(int N, fsp_dtype dtype, fsp_stream stream, int *lgL_row, int *lgL_col) {
+    fsp_status st = validate_size(N, 1.0, FSP_HE);
+    if (st != FSP_OK) return st;
+    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED) return FSP_EINVAL;  // generic engine only
+    fsp_plan *p = nullptr;
+    if ((st = plan_create_impl(&p, N, 1.0, 1.0 / N, FSP_HE, dtype, stream, true)) != FSP_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)N * N * N * p->rsize;
+    DevBuf rho, phi;
+    if ((st = alloc_or_nomem(rho, bytes)) != FSP_OK || (st = alloc_or_nomem(phi, bytes)) != FSP_OK) {
+        fsp_plan_destroy(p);
+        return st;
+    }
+    cudaMemsetAsync(rho.p, 0, bytes, s);
+    // enough solves per round for a few milliseconds of work
+    const int reps = std::max(2, std::min(200, (int)(4e6 / ((double)N * N * N))));
+    int best_r = p->row.lgL, best_c = p->col.lgL;
+    double best = time_generic(p, best_r, best_c, rho.p, phi.p, s, reps);
+    for (int lr = 0; lr <= 5; ++lr) {  // rows, columns at their current best
+        const double t = time_generic(p, lr, best_c, rho.p, phi.p, s, reps);
+        if (t > 0 && t < best) best = t, best_r = lr;
+    }
+    for (int lc = 0; lc <= 5; ++lc) {
+        const double t = time_generic(p, best_r, lc, rho.p, phi.p, s, reps);
+        if (t > 0 && t < best) best = t, best_c = lc;
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    fsp_plan_destroy(p);
+    if (e != cudaSuccess || best <= 0 || best >= 1e30) return FSP_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuning[{N, (int)dtype}] = {best_r, best_c};
+    }
+    if (lgL_row) *lgL_row = best_r;
+    if (lgL_col) *lgL_col = best_c;
+    return FSP_OK;
+}
+
+// Table text: one entry per line, "N dtype lgL_row lgL_col".
+extern "C" fsp_status fsp_tuning_get(char *buf, size_t cap, size_t *len) {
+    std::string out;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &kv : g_tuning)
+            out += std::to_string(kv.first.first) + " " + std::to_string(kv.first.second) + " " +
+                   std::to_string(kv.second.first) + " " + std::to_string(kv.second.second) + "\n";
+    }
+    if (len) *len = out.size() + 1;
+    if (!buf) return FSP_OK;
+    if (cap < out.size() + 1) return FSP_EINVAL;
+    std::memcpy(buf, out.c_str(), out.size() + 1);
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_tuning_set(const char *text) {
+    if (!text) return FSP_EINVAL;
+    std::map<std::pair<int, int>, std::pair<int, int>> t;
+    const char *c = text;
+    while (*c) {
+        int N, dt, lr, lc, used = 0;
+        if (std::sscanf(c, " %d %d %d %d%n", &N, &dt, &lr, &lc, &used) != 4) {
+            while (*c == ' ' || *c == '\n' || *c == '\t' || *c == '\r') ++c;
+            if (*c) return FSP_EINVAL;
+            break;
+        }
+        if (N < 2 || N > kMaxN || (dt != FSP_F64 && dt != FSP_F32_MIXED) || lr < 0 || lr > 5 || lc < 0 || lc > 5)
+            return FSP_EINVAL;
+        t[{N, dt}] = {lr, lc};
+        c += used;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : t) g_tuning[kv.first] = kv.second;
+    return FSP_OK;
 }

@@ -117,6 +117,18 @@ fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stre
  */
 fsp_status fsp_solve_host(fsp_plan *plan, const void *rho_host, void *phi_host, fsp_stream stream);
 
+/*
+ * fsp_solve_host_many -- `count` solves of HOST arrays, pipelined: the copy of
+ * source i+1 to the device and the copy of result i-1 back to the host run on
+ * their own streams while solve i runs on `stream`, through two device
+ * staging pairs.  rho_host[i], phi_host[i]: host pointers (pinned for
+ * asynchronous, full-bandwidth copies), N^3 reals of the plan's dtype.  The
+ * first call allocates four N^3 staging buffers, two streams and six events,
+ * kept by the plan.  Returns after every result is on the host.
+ */
+fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void *const *phi_host, int count,
+                               fsp_stream stream);
+
 /* Wait for all work enqueued for this plan's solves and report any
  * asynchronous CUDA error as FSP_ECUDA. */
 fsp_status fsp_plan_sync(fsp_plan *plan, fsp_stream stream);

@@ -61,6 +61,8 @@ def lib(build_if_missing=True):
     L.fsp_plan_create.argtypes = [ctypes.POINTER(vp), i, d, d, i, i, vp]
     L.fsp_solve.argtypes = [vp, vp, vp, vp]
     L.fsp_solve_host.argtypes = [vp, vp, vp, vp]
+    L.fsp_solve_host_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
+    L.fsp_solve_host_many.restype = i
     L.fsp_plan_sync.argtypes = [vp, vp]
     L.fsp_plan_destroy.argtypes = [vp]
     L.fsp_plan_bytes.argtypes = [vp]
@@ -184,6 +186,15 @@ class Plan:
         check(lib().fsp_solve_host(self._p, ctypes.c_void_p(rp), ctypes.c_void_p(pp), _stream_handle(stream)),
               "fsp_solve_host")
         return phi_host
+
+    def solve_host_many(self, rhos_host, phis_host, stream=None):
+        """Pipelined solves of host arrays (copies overlap the solves)."""
+        def ptr(t):
+            return t.data_ptr() if hasattr(t, "data_ptr") else t.ctypes.data
+        check(lib().fsp_solve_host_many(self._p, _ptr_array([ptr(r) for r in rhos_host]),
+                                        _ptr_array([ptr(f) for f in phis_host]), len(rhos_host),
+                                        _stream_handle(stream)), "fsp_solve_host_many")
+        return phis_host
 
     def spectrum(self):
         import numpy as np

@@ -283,6 +283,10 @@ struct fsp_plan {
     size_t rsize = 8;  // bytes per real
     void *S = nullptr, *W1 = nullptr, *W2 = nullptr, *tw_n = nullptr, *tw_2n = nullptr;
     void *stage_rho = nullptr, *stage_phi = nullptr;
+    // pipelined host solves: two staging pairs, copy streams, events
+    void *pipe_rho[2] = {}, *pipe_phi[2] = {};
+    cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
     TileCfg row, col;
     bool fast = false;  // specialised power-of-two kernels (fast.cuh) serve this N
     cudaEvent_t ev[6] = {};
@@ -299,8 +303,14 @@ bool plan_live(const fsp_plan *p) {
 }
 
 void plan_free(fsp_plan *p) {
-    for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi})
+    for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi, p->pipe_rho[0], p->pipe_rho[1],
+                    p->pipe_phi[0], p->pipe_phi[1]})
         if (q) cudaFree(q);
+    for (cudaStream_t q : {p->pipe_h2d, p->pipe_d2h})
+        if (q) cudaStreamDestroy(q);
+    for (int i = 0; i < 2; ++i)
+        for (cudaEvent_t q : {p->ev_in[i], p->ev_comp[i], p->ev_out[i]})
+            if (q) cudaEventDestroy(q);
     p->magic = 0;
     delete p;
 }
@@ -539,6 +549,72 @@ fsp_status fsp_solve_host(fsp_plan *plan, const void *rho_host, void *phi_host, 
     if (st != FSP_OK) return st;
     FSP_TRY_CUDA(cudaMemcpyAsync(phi_host, plan->stage_phi, bytes, cudaMemcpyDeviceToHost, s));
     return cuda_status(cudaStreamSynchronize(s));
+}
+
+fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void *const *phi_host, int count,
+                               fsp_stream stream) {
+    if (!plan_live(plan) || count < 0 || (count > 0 && (!rho_host || !phi_host))) return FSP_EINVAL;
+    if (!plan->W1) return FSP_EINVAL;
+    for (int i = 0; i < count; ++i)
+        if (!rho_host[i] || !phi_host[i]) return FSP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    if (dev != plan->device) return FSP_EINVAL;
+    if (count == 0) return FSP_OK;
+    const size_t bytes = (size_t)plan->N * plan->N * plan->N * plan->rsize;
+    if (!plan->pipe_h2d) {  // first use: staging pairs, copy streams, events
+        DevBuf a0, a1, b0, b1;
+        fsp_status st;
+        if ((st = alloc_or_nomem(a0, bytes)) != FSP_OK || (st = alloc_or_nomem(a1, bytes)) != FSP_OK ||
+            (st = alloc_or_nomem(b0, bytes)) != FSP_OK || (st = alloc_or_nomem(b1, bytes)) != FSP_OK)
+            return st;
+        cudaStream_t h2d = nullptr, d2h = nullptr;
+        cudaEvent_t ev[6] = {};
+        bool ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 6 && ok; ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            for (cudaStream_t q : {h2d, d2h})
+                if (q) cudaStreamDestroy(q);
+            for (cudaEvent_t q : ev)
+                if (q) cudaEventDestroy(q);
+            return FSP_ECUDA;
+        }
+        plan->pipe_rho[0] = a0.release(), plan->pipe_rho[1] = a1.release();
+        plan->pipe_phi[0] = b0.release(), plan->pipe_phi[1] = b1.release();
+        plan->pipe_h2d = h2d, plan->pipe_d2h = d2h;
+        for (int i = 0; i < 2; ++i) plan->ev_in[i] = ev[i], plan->ev_comp[i] = ev[2 + i], plan->ev_out[i] = ev[4 + i];
+        plan->bytes += 4 * bytes;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // all three streams start after prior work on `stream`
+    cudaError_t e = cudaEventRecord(plan->ev_out[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->pipe_h2d, plan->ev_out[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->pipe_d2h, plan->ev_out[0], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_comp[0], s);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_comp[1], s);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[1], s);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        const int k = i & 1;
+        // copy in: slot k's source buffer is free once the solve of i-2 ran
+        e = cudaStreamWaitEvent(plan->pipe_h2d, plan->ev_comp[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(plan->pipe_rho[k], rho_host[i], bytes, cudaMemcpyHostToDevice, plan->pipe_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_in[k], plan->pipe_h2d);
+        // solve: after its copy-in and after the copy-out of i-2 freed slot k
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->ev_in[k], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->ev_out[k], 0);
+        if (e == cudaSuccess) e = enqueue_solve_ws(plan, plan->pipe_rho[k], plan->pipe_phi[k], plan->W1, plan->W2, s);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_comp[k], s);
+        // copy out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->pipe_d2h, plan->ev_comp[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(phi_host[i], plan->pipe_phi[k], bytes, cudaMemcpyDeviceToHost, plan->pipe_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[k], plan->pipe_d2h);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(plan->pipe_d2h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
 }
 
 fsp_status fsp_plan_sync(fsp_plan *plan, fsp_stream stream) {

@@ -145,3 +145,18 @@ def test_plan_accounting(fsp):
     expect = (N + 1) ** 2 * P * 8 + 3 * N * N * P * 16 + 3 * N * 16
     assert p.bytes == expect
     assert p.precompute_ms > 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64df"])
+def test_solve_host_many_matches_device(fsp, dtype):
+    import torch
+    N = 64
+    p = fsp.Plan(N, 1.0, "vg_dct", dtype)
+    srcs = [I.gaussian_mixture(N, seed=s) for s in range(5)]
+    tdt = fsp.torch_dtype(dtype)
+    hin = [torch.from_numpy(x).to(tdt).pin_memory() for x in srcs]
+    hout = [torch.empty_like(h).pin_memory() for h in hin]
+    p.solve_host_many(hin, hout)
+    for h, o in zip(hin, hout):
+        assert torch.equal(o, p.solve(h.cuda()).cpu())
+    p.solve_host_many([], [])  # nothing to do

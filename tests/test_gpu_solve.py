@@ -160,3 +160,19 @@ def test_solve_host_many_matches_device(fsp, dtype):
     for h, o in zip(hin, hout):
         assert torch.equal(o, p.solve(h.cuda()).cpu())
     p.solve_host_many([], [])  # nothing to do
+
+
+@pytest.mark.parametrize("algo,dtype,tol", [("vg", "f64", 1e-5), ("vg_dct", "f64df", 1e-5), ("vg_dct", "f32", 1e-4)])
+def test_far_field_uses_the_full_window(fsp, algo, dtype, tol):
+    """Off-centre Gaussian (sigma 0.04 at (-0.3,-0.3,-0.3)) against its analytic
+    potential more than 1.2 away: the device's truncation window must exceed
+    the box diagonal (Sec. 2.3)."""
+    from oracle import analytic as A
+    N, c, s = 32, (-0.3, -0.3, -0.3), 0.04
+    p = fsp.Plan(N, 1.0, algo, dtype)
+    phi = p.solve(to_dev(I.gaussian(N, 1.0, s, c), dtype)).double().cpu().numpy()
+    ex = A.gaussian_potential(N, 1.0, s, c)
+    x = I.cell_centres(N, 1.0)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    far = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) > 1.2
+    assert np.max(np.abs(phi[far] - ex[far]) / ex[far]) < tol

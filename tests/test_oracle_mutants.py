@@ -1,0 +1,136 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (a flipped
+transform sign, a wrong twiddle index, a dropped factor or scale, an
+off-by-one in the frequency grid or the mirror fold, a wrong window or series
+coefficient, a wrong stride, a padding bound), builds it with gcc on the CPU
+and runs the pins against it: at least one must fail.  The mistakes are made
+in a temporary copy; the oracle itself is never modified.
+"""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+import scipy.fft
+
+import fsp_inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(os.path.dirname(HERE), "oracle", "fsp_oracle.c")
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("fft_direction", "return sign < 0 ? w : conj(w);", "return sign > 0 ? w : conj(w);"),
+    ("twiddle_index", "root_of(R, n, (long long)r * k, sign)", "root_of(R, n, (long long)r * (k + 1), sign)"),
+    ("dct_interior_factor", "acc += 2.0 * src[j] * c[((long long)j * k) % (2 * M)];\n            dst[k] = acc;",
+     "acc += 1.0 * src[j] * c[((long long)j * k) % (2 * M)];\n            dst[k] = acc;"),
+    ("dct_endpoint_sign", "double acc = src[0] + ((k & 1) ? -src[M] : src[M]);\n            for (int j = 1; j < M; ++j) acc += 2.0 * src[j] * c[((long long)j * k) % (2 * M)];\n            dst[k] = acc;",
+     "double acc = src[0] + src[M];\n            for (int j = 1; j < M; ++j) acc += 2.0 * src[j] * c[((long long)j * k) % (2 * M)];\n            dst[k] = acc;"),
+    ("vg_scale_power", "double scale = 1.0 / (((double)n4 * h) * ((double)n4 * h) * ((double)n4 * h));",
+     "double scale = 1.0 / (((double)n4 * h) * ((double)n4 * h));"),
+    ("vg_negative_freq_offset", "int jx = sx < 2 * N ? sx : sx - n4;", "int jx = sx < 2 * N ? sx : sx - n4 + 1;"),
+    ("he_origin_value", ": 1.0 / (4.0 * ORC_PI);", ": 0.0;"),
+    ("mirror_fold", "static inline int fold2(int m, int N) { return m <= N ? m : 2 * N - m; }",
+     "static inline int fold2(int m, int N) { return m < N ? m : 2 * N - m - 1; }"),
+    ("solve_scale", "double scale = h * h * h / (double)tot;\n    for (int z = 0; z < N; ++z)",
+     "double scale = h * h / (double)tot;\n    for (int z = 0; z < N; ++z)"),
+    ("vg_window", "double Lt = alpha * sqrt(3.0) * L;", "double Lt = alpha * L;"),
+    ("sinc_series", "s = 1.0 - u * u / 6.0 + u * u * u * u / 120.0;", "s = 1.0 - u * u / 3.0 + u * u * u * u / 120.0;"),
+    ("fft3d_stride", "ptrdiff_t strides[3] = {1, nx, (ptrdiff_t)nx * ny};", "ptrdiff_t strides[3] = {1, ny, (ptrdiff_t)nx * ny};"),
+    ("direct_sum_h3", "out[p] = h * h * h * (sum + comp);", "out[p] = h * h * (sum + comp);"),
+    ("padding_bound", "for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 0; x < N; ++x) r2[",
+     "for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 1; x < N; ++x) r2["),
+]
+
+
+def _build(name, old, new, tmp):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutation target not found: " + name
+    path = os.path.join(tmp, name + ".c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new, 1))
+    lib = os.path.join(tmp, "lib_" + name + ".so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", lib, path, "-lm"], check=True)
+    return lib
+
+
+def _pins(orc):
+    """Name -> passed, for a cheap set of the oracle's pins."""
+    from oracle import analytic as A
+    res = {}
+    r = np.random.default_rng(0)
+    x = r.standard_normal(30) + 1j * r.standard_normal(30)
+    res["fft_vs_pocketfft"] = np.allclose(orc.fft1d(x, -1), np.fft.fft(x), atol=1e-12) and \
+        np.allclose(orc.fft1d(x, 1), np.fft.ifft(x) * 30, atol=1e-12)
+    a = r.standard_normal((6, 10, 12)) + 0j
+    res["fft3d_vs_fftn"] = np.allclose(orc.fft3d(a, -1), np.fft.fftn(a), atol=1e-11)
+    g = r.standard_normal((9, 9, 9))
+    res["dct1_vs_scipy"] = np.allclose(orc.dct1_3d(g, 4), scipy.fft.dctn(g, type=1)[:5, :5, :5], atol=1e-10)
+    Lt = 1.905
+    u = 5e-4
+    k = 2 * u / Lt
+    ref = 2 * (np.sin(u) / u) ** 2 * (Lt / 2) ** 2
+    res["vico_hat"] = abs(orc.green_vico_hat(k, Lt) - ref) < 1e-14 * ref
+    full, T = orc.vg_full(4)
+    res["vg_sum_rule"] = abs((0.25 ** 3) * full.real.sum() - orc.window(1.0) ** 2 / 2) < 1e-10
+    res["vg_equals_vg_dct"] = np.allclose(orc.kernel_T("vg", 4), orc.kernel_T("vg_dct", 4), rtol=1e-12, atol=1e-14)
+    for algo in ("he", "vg_dct"):
+        T = orc.kernel_T(algo, 6)
+        rho = I.random_field(6, 1)
+        res["fft_eq_direct_" + algo] = np.allclose(orc.solve_fft(T, rho, 1 / 6), orc.solve_direct(T, rho, 1 / 6),
+                                                   rtol=1e-12, atol=1e-14)
+    N = 8
+    phi = orc.solve("he", I.impulse(N, 1.0, (0, 0, 0)))
+    z, y, x3 = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    d = np.sqrt(x3 ** 2 + y ** 2 + z ** 2)
+    imp = np.where(d > 0, 1 / (4 * np.pi * (1 / N) * np.maximum(d, 1e-300)), 1 / (4 * np.pi))
+    res["he_impulse"] = np.allclose(phi, imp, rtol=1e-12)
+    e_vg = A.rel_l2(orc.solve("vg", I.gaussian(16)), A.gaussian_potential(16))
+    res["gauss_vg16"] = 1e-4 <= e_vg <= 1e-2
+    res["vg_far_field"] = _far_field_err(orc, "vg_dct", 16) < 1e-2
+    return res
+
+
+def _far_field_err(orc, algo, N, c=(-0.3, -0.3, -0.3), s=0.04):
+    """Max relative error of the potential of an off-centre Gaussian at the
+    points more than 1.2 from it (beyond a truncation window shorter than the
+    box diagonal)."""
+    from oracle import analytic as A
+    phi = orc.solve(algo, I.gaussian(N, 1.0, s, c))
+    ex = A.gaussian_potential(N, 1.0, s, c)
+    x = I.cell_centres(N, 1.0)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    far = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) > 1.2
+    return float(np.max(np.abs(phi[far] - ex[far]) / ex[far]))
+
+
+@pytest.fixture(scope="module")
+def baseline(orc):
+    return _pins(orc)
+
+
+def test_pins_pass_on_the_oracle(baseline):
+    assert all(baseline.values()), baseline
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(orc, name, old, new):
+    with tempfile.TemporaryDirectory() as tmp:
+        path = _build(name, old, new, tmp)
+        saved = orc._lib
+        try:
+            orc._lib = None
+            mutant = ctypes.CDLL(path)
+            orig_build = orc._build.build
+            orc._build.build = lambda force=False: path  # load the mutant instead
+            orc._load()
+            res = _pins(orc)
+        finally:
+            orc._build.build = orig_build
+            orc._lib = saved
+        del mutant
+    failed = [k for k, ok in res.items() if not ok]
+    assert failed, "no pin caught the planted mistake " + name

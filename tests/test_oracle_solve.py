@@ -99,6 +99,23 @@ def test_vg_spectral(orc, algo):
     assert e32 < 1e-8
 
 
+@pytest.mark.parametrize("algo", ALGOS)
+def test_far_field_of_off_centre_gaussian(orc, algo):
+    """Sec. 2.3: the truncation window must exceed every separation in the box.
+    A Gaussian (sigma 0.04, centred at (-0.3,-0.3,-0.3), five sigma inside the
+    faces) evaluated more than 1.2 away (up to the far corner, about 1.39):
+    a window shorter than that would zero the potential there."""
+    from oracle import analytic as A
+    N, c, s = 24, (-0.3, -0.3, -0.3), 0.04
+    phi = orc.solve(algo, I.gaussian(N, 1.0, s, c))
+    ex = A.gaussian_potential(N, 1.0, s, c)
+    x = I.cell_centres(N, 1.0)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    far = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) > 1.2
+    assert far.sum() > 50
+    assert np.max(np.abs(phi[far] - ex[far]) / ex[far]) < 1e-4
+
+
 @pytest.mark.parametrize("algo", ["he", "vg_dct"])
 def test_sphere_is_not_spectral(orc, algo):
     from oracle import analytic as A

@@ -292,9 +292,22 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int l = threadIdx.x % L, t = threadIdx.x / L;
-    const int line = blockIdx.x * L + l;
-    const bool ok = line <= N;
-    const long long bt = blockIdx.y;
+    // Main tiles: lines (k_x) [bx*L, bx*L + L) of batch row by - X, all < N.
+    // The Nyquist column k_x = N runs in the first X = NB/N block rows, whose
+    // tile's L lines are L consecutive batch indices of that one column (their
+    // loads are strided, so they go first rather than form the last wave).
+    constexpr int NB = MODE == COL_FMI ? 2 * N : N;  // batch rows (k_y or z)
+    constexpr int X = NB / N;
+    int line;
+    long long bt;
+    if ((int)blockIdx.y >= X) {
+        line = blockIdx.x * L + l;
+        bt = blockIdx.y - X;
+    } else {
+        line = N;
+        bt = ((long long)blockIdx.y * (N / L) + blockIdx.x) * L + l;
+    }
+    constexpr bool ok = true;
     const C *tw = reinterpret_cast<const C *>(a.tw);
     // thread-relative bases: position p = t + c lives at base_t + c*POS
     const C *in_t = reinterpret_cast<const C *>(a.in) + bt * G::IN_BATCH + line + (long long)t * G::IN_POS;
@@ -543,7 +556,11 @@ template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a
         const size_t sm = smem_for<T, n>(n);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)((a.nlines + K::L - 1) / K::L), (unsigned)nbatch);
+        // N/L full tiles per batch row, plus nbatch/N block rows of Nyquist tiles
+        constexpr int N = n / 2;
+        static_assert(N % K::L == 0, "tiles must cover k_x < N exactly");
+        if (nbatch % N != 0) return cudaErrorInvalidValue;
+        dim3 grid((unsigned)(N / K::L), (unsigned)(nbatch + nbatch / N));
         kern<<<grid, K::L * (n / K::V), sm, s>>>(a);
         return cudaGetLastError();
     }

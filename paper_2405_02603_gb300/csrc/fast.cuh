@@ -400,13 +400,21 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_r2c(const RowArgs a) {
     const long long row0 = (long long)blockIdx.x * L;
     using R = typename io_of<T>::t;
     const R *x = reinterpret_cast<const R *>(a.x);
-    // coalesced row loads of the packed pairs (x[2m], x[2m+1]), m < N/2
-#pragma unroll 4
-    for (int idx = tid; idx < L * H; idx += NTH) {
-        const int m = idx % H, rr = idx / H;
-        C z = C{T(0), T(0)};
-        if (row0 + rr < a.nrows) z = load_pair<T>(x + (row0 + rr) * N, m);
-        buf[m * LD + rr] = z;
+    // coalesced row loads of the packed pairs (x[2m], x[2m+1]), m < N/2, all
+    // of a thread's loads issued before the first shared-memory store
+    {
+        constexpr int PER = (L * H + NTH - 1) / NTH;
+        C q[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = tid + i * NTH, m = idx % H, rr = idx / H;
+            q[i] = idx < L * H && row0 + rr < a.nrows ? load_pair<T>(x + (row0 + rr) * N, m) : C{T(0), T(0)};
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = tid + i * NTH;
+            if (idx < L * H) buf[(idx % H) * LD + idx / H] = q[i];
+        }
     }
     __syncthreads();
     const C *tw = reinterpret_cast<const C *>(a.tw);
@@ -463,13 +471,33 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int tid = threadIdx.x, l = tid % L, t = tid / L;
     const long long row0 = (long long)blockIdx.x * L;
-    // one warp per row: coalesced loads of the N+1 coefficients
+    // one warp per row: coalesced loads of the N+1 coefficients, all of a
+    // thread's loads issued before the first shared-memory store
     const C *c = reinterpret_cast<const C *>(a.c);
     const int warp = tid >> 5, lane = tid & 31;
-    for (int rr = warp; rr < L; rr += NTH / 32) {
-        const bool okr = row0 + rr < a.nrows;
-        const C *crow = c + (row0 + rr) * row_pitch(N);
-        for (int k = lane; k <= N; k += 32) buf[k * LD + rr] = okr ? crow[k] : C{T(0), T(0)};
+    {
+        constexpr int NW = NTH / 32, RPW = (L + NW - 1) / NW, KPL = (N + 32) / 32;
+        C q[RPW * KPL];
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const int rr = warp + i * NW;
+            const bool okr = rr < L && row0 + rr < a.nrows;
+            const C *crow = c + (okr ? row0 + rr : 0) * row_pitch(N);
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const int k = lane + 32 * j;
+                q[i * KPL + j] = okr && k <= N ? crow[k] : C{T(0), T(0)};
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const int rr = warp + i * NW;
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const int k = lane + 32 * j;
+                if (rr < L && k <= N) buf[k * LD + rr] = q[i * KPL + j];
+            }
+        }
     }
     __syncthreads();
     // Z[k] = A + i conj(w^k) B, Z[N-k] = conj A + i w^k conj B
@@ -531,7 +559,7 @@ FSP_CFG(double, 1024, 16, 8, 16, 8, 8)
 FSP_CFG(df, 32, 8, 16, 4, 8, 1)
 FSP_CFG(df, 64, 8, 16, 8, 8, 1)
 FSP_CFG(df, 128, 16, 8, 8, 16, 1)
-FSP_CFG(df, 256, 16, 8, 16, 16, 1)
+FSP_CFG(df, 256, 8, 8, 8, 8, 4)
 FSP_CFG(df, 512, 8, 8, 8, 8, 8)
 FSP_CFG(df, 1024, 16, 8, 16, 8, 8)
 #undef FSP_CFG

@@ -18,7 +18,13 @@ error metrics.  Every function names the passage of the paper it follows:
 - ``solve_direct``: the O(N_g^2) discrete convolution sum (Sec. 1).
 - ``spectrum``: the multiplier h^3 DFT{G_2}/(2N)^3 on the non-redundant octant.
 - ``analytic``: the Gaussian (Sec. 3.1, Eq. gaussian) and uniform-sphere
-  (Sec. 3.1, Eq. sphere) potentials, in this project's sign convention.
+  (Sec. 3.1, Eq. sphere) potentials, in this project's sign convention, and
+  the Gaussian's field.
+- ``dst1``/``trig1_3d``: type-I DST by definition, and the separable 3D
+  DST-I/DCT-I mix an odd kernel's octant needs.
+- ``field_kernel``, ``solve_field_fft``, ``solve_field_direct``,
+  ``field_spectrum``, ``solve_field``: the field E = -grad phi (Appendix B,
+  Eq. efield) as the convolution of rho with F = -grad G of each method.
 """
 import ctypes
 
@@ -55,6 +61,12 @@ def _load():
         lib.orc_solve_fft.argtypes = [i, d, dp, dp, dp]
         lib.orc_spectrum.argtypes = [i, d, dp, dp]
         lib.orc_solve_direct.argtypes = [i, d, dp, dp, lp, ctypes.c_longlong, dp]
+        lib.orc_dst1_1d.argtypes = [i, dp, dp]
+        lib.orc_trig1_3d.argtypes = [i, i, i, dp, dp]
+        lib.orc_field_kernel.argtypes = [i, i, i, d, d, dp]
+        lib.orc_solve_field_fft.argtypes = [i, d, i, dp, dp, dp]
+        lib.orc_field_spectrum.argtypes = [i, d, i, dp, dp]
+        lib.orc_solve_field_direct.argtypes = [i, d, i, dp, dp, lp, ctypes.c_longlong, dp]
         _lib = lib
     return _lib
 
@@ -193,9 +205,84 @@ def solve(algo, rho, L=1.0, alpha=ALPHA):
     return solve_fft(T, rho, L / N)
 
 
+def dst1(x):
+    """Unnormalised DST-I on the interior of x[0..M] (RODFT00), by definition;
+    returns X[0..M] with X[0] = X[M] = 0."""
+    x = _f64(x)
+    out = np.empty_like(x)
+    _load().orc_dst1_1d(x.size - 1, _p(x), _p(out))
+    return out
+
+
+def trig1_3d(x, odd, K=None):
+    """DST-I along axis `odd` (0 = x, 1 = y, 2 = z; array index order [z,y,x])
+    and DCT-I along the others of a (M+1)^3 array, outputs [0,K]^3."""
+    x = _f64(x)
+    M = x.shape[0] - 1
+    assert x.shape == (M + 1,) * 3
+    K = M if K is None else int(K)
+    out = np.empty((K + 1,) * 3, dtype=np.float64)
+    _load().orc_trig1_3d(M, K, int(odd), _p(x), _p(out))
+    return out
+
+
+def field_kernel(algo, a, N, L=1.0, alpha=ALPHA):
+    """Field kernel F_a[m] = -dG/dx_a at m h, m in [0,N]^3, component a
+    (0 = x, 1 = y, 2 = z), shape (N+1,)*3 indexed [z,y,x]."""
+    algo = ALGOS.get(algo, algo)
+    F = np.empty((N + 1,) * 3, dtype=np.float64)
+    _load().orc_field_kernel(int(algo), int(a), int(N), float(L), float(alpha), _p(F))
+    return F
+
+
+def solve_field_fft(F, a, rho, h):
+    """E_a = h^3 sum_j F_a[i-j] rho_j on the full doubled grid (odd kernel)."""
+    F, rho = _f64(F), _f64(rho)
+    N = rho.shape[0]
+    assert rho.shape == (N, N, N) and F.shape == (N + 1,) * 3
+    E = np.empty_like(rho)
+    _load().orc_solve_field_fft(N, float(h), int(a), _p(F), _p(rho), _p(E))
+    return E
+
+
+def field_spectrum(F, a, h):
+    """S_a[q] = -h^3 Im DFT_{2N}{F_2}[q] / (2N)^3 for q in [0,N]^3."""
+    F = _f64(F)
+    N = F.shape[0] - 1
+    S = np.empty_like(F)
+    _load().orc_field_spectrum(N, float(h), int(a), _p(F), _p(S))
+    return S
+
+
+def solve_field_direct(F, a, rho, h, points=None):
+    """E_a[i] = h^3 sum_j sgn(i_a - j_a) F_a[|i-j|] rho_j, at flat indices
+    `points` (or all)."""
+    F, rho = _f64(F), _f64(rho)
+    N = rho.shape[0]
+    assert rho.shape == (N, N, N) and F.shape == (N + 1,) * 3
+    lib = _load()
+    if points is None:
+        out = np.empty_like(rho)
+        lib.orc_solve_field_direct(N, float(h), int(a), _p(F), _p(rho), None, 0, _p(out))
+        return out
+    pts = np.ascontiguousarray(points, dtype=np.int64).ravel()
+    assert pts.size == 0 or (pts.min() >= 0 and pts.max() < N ** 3)
+    out = np.empty(pts.size, dtype=np.float64)
+    lib.orc_solve_field_direct(N, float(h), int(a), _p(F), _p(rho),
+                               pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), pts.size, _p(out))
+    return out
+
+
+def solve_field(algo, rho, L=1.0, alpha=ALPHA):
+    """(E_x, E_y, E_z) for one source: field kernels plus FFT solves."""
+    N = rho.shape[0]
+    return tuple(solve_field_fft(field_kernel(algo, a, N, L, alpha), a, rho, L / N) for a in range(3))
+
+
 from . import analytic  # noqa: E402  (pure-numpy helpers, no C)
 
 __all__ = ["HE", "VG", "VG_DCT", "ALPHA", "dft1d", "fft1d", "fft3d", "dct1", "dct1_3d",
            "green_vico_hat", "window", "kernel_T", "vg_full", "spectrum", "solve_fft",
-           "solve_direct", "solve", "analytic", "num_threads", "set_num_threads"]
+           "solve_direct", "solve", "analytic", "num_threads", "set_num_threads", "dst1", "trig1_3d",
+           "field_kernel", "solve_field_fft", "field_spectrum", "solve_field_direct", "solve_field"]
 

@@ -64,3 +64,20 @@ def rel_l2(phi, ref):
     phi = np.asarray(phi, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return float(np.linalg.norm((phi - ref).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+def gaussian_field(N, L=1.0, sigma=0.05, centre=(0.0, 0.0, 0.0), weight=1.0):
+    """Field E = -grad phi of weight * (unit-charge Gaussian of width sigma):
+    radial, E_r(r) = weight * Q(r) / (4 pi r^2) with the enclosed charge
+    Q(r) = erf(r / (sqrt(2) sigma)) - sqrt(2/pi) (r/sigma) exp(-r^2 / (2 sigma^2))
+    (Gauss's law), zero at the centre.  Returns (E_x, E_y, E_z), each of shape
+    (N, N, N) indexed [z, y, x]."""
+    c = cell_centres(N, L)
+    z = np.broadcast_to(c[:, None, None] - centre[2], (N, N, N))
+    y = np.broadcast_to(c[None, :, None] - centre[1], (N, N, N))
+    x = np.broadcast_to(c[None, None, :] - centre[0], (N, N, N))
+    r = np.sqrt(x * x + y * y + z * z)
+    s = r / sigma
+    q = erf(s / np.sqrt(2.0)) - np.sqrt(2.0 / np.pi) * s * np.exp(-0.5 * s * s)
+    er_over_r = np.where(r > 1e-12, q / (4.0 * np.pi * np.maximum(r, 1e-300) ** 3), 0.0)
+    return tuple(weight * er_over_r * d for d in (x, y, z))

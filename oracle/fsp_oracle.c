@@ -28,6 +28,11 @@
  *                        G_2, multiply, inverse FFT, scale by h^3, restrict.
  *   - orc_solve_direct : the discrete convolution phi_i = h^3 sum_j T[i-j] rho_j
  *                        evaluated term by term (Sec. 1, the O(N_g^2) sum).
+ *   - orc_dst1_1d, orc_trig1_3d, orc_field_kernel, orc_solve_field_fft,
+ *     orc_field_spectrum, orc_solve_field_direct : the field E = -grad phi of
+ *                        Appendix B (Eq. efield), as the convolution of rho
+ *                        with the field kernel F = -grad G of each method (the
+ *                        field-kernel reading is stated at orc_field_kernel).
  *
  * Conventions (the readings of the paper this oracle takes):
  *   - Sign: G = +1/(4 pi |x|) with eps0 = 1 (Sec. 1, Eq. convolution_eq), so
@@ -259,6 +264,68 @@ void orc_dct1_3d(int M, int K, const double *x, double *X) {
     free(c);
 }
 
+/* ------------------------------------------------------------- DST-I -- */
+/*
+ * Unnormalised type-I DST of the M-1 interior samples of x[0..M] (FFTW
+ * RODFT00 convention, the two zero end points kept in place):
+ *   X[k] = 2 sum_{j=1}^{M-1} x[j] sin(pi j k / M),  k in [0,M]  (X[0] = X[M] = 0).
+ * x[0] and x[M] are not read.  It is the DFT of length 2M of the odd
+ * extension of x, divided by -i.
+ */
+void orc_dst1_1d(int M, const double *x, double *X) {
+    for (int k = 0; k <= M; ++k) {
+        double acc = 0.0;
+        for (int j = 1; j < M; ++j) acc += 2.0 * x[j] * sin(ORC_PI * (double)(((long long)j * k) % (2 * M)) / M);
+        X[k] = acc;
+    }
+}
+
+/*
+ * One axis of a separable transform of a 3D array (x fastest): every line
+ * along `axis` (0 = x, 1 = y, 2 = z) of M+1 samples is replaced by its DCT-I
+ * (kind 0) or DST-I (kind 1), evaluated at outputs [0,K].  in has extents
+ * (nx, ny, nz); out has the same extents except K+1 along `axis`.
+ */
+static void axis_trig(int M, int K, int kind, int axis, int nx, int ny, int nz, const double *in, double *out) {
+    int ext[3] = {nx, ny, nz}, oext[3] = {nx, ny, nz};
+    oext[axis] = K + 1;
+    size_t istr[3] = {1, (size_t)nx, (size_t)nx * ny};
+    size_t ostr[3] = {1, (size_t)oext[0], (size_t)oext[0] * oext[1]};
+    int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;  /* the two other axes */
+    double *tab = (double *)malloc(sizeof(double) * (size_t)(2 * M));
+    for (int e = 0; e < 2 * M; ++e) tab[e] = kind == 0 ? cos(ORC_PI * (double)e / M) : sin(ORC_PI * (double)e / M);
+    long long lines = (long long)ext[a1] * ext[a2];
+#pragma omp parallel for schedule(static)
+    for (long long L = 0; L < lines; ++L) {
+        int u = (int)(L % ext[a1]), v = (int)(L / ext[a1]);
+        const double *src = in + (size_t)u * istr[a1] + (size_t)v * istr[a2];
+        double *dst = out + (size_t)u * ostr[a1] + (size_t)v * ostr[a2];
+        size_t si = istr[axis], so = ostr[axis];
+        for (int k = 0; k <= K; ++k) {
+            double acc = kind == 0 ? src[0] + ((k & 1) ? -src[(size_t)M * si] : src[(size_t)M * si]) : 0.0;
+            for (int j = 1; j < M; ++j) acc += 2.0 * src[(size_t)j * si] * tab[((long long)j * k) % (2 * M)];
+            dst[(size_t)k * so] = acc;
+        }
+    }
+    free(tab);
+}
+
+/*
+ * 3D transform of a (M+1)^3 array: DST-I along axis `odd` (0 = x, 1 = y,
+ * 2 = z) and DCT-I along the two others (odd < 0: DCT-I along all three),
+ * evaluated at outputs [0,K]^3 (K <= M).  Returns a (K+1)^3 array.
+ */
+void orc_trig1_3d(int M, int K, int odd, const double *x, double *X) {
+    int n = M + 1, k1 = K + 1;
+    double *t1 = (double *)malloc(sizeof(double) * (size_t)n * n * k1);
+    double *t2 = (double *)malloc(sizeof(double) * (size_t)n * k1 * k1);
+    axis_trig(M, K, odd == 0, 0, n, n, n, x, t1);
+    axis_trig(M, K, odd == 1, 1, k1, n, n, t1, t2);
+    axis_trig(M, K, odd == 2, 2, k1, k1, n, t2, X);
+    free(t2);
+    free(t1);
+}
+
 /* ------------------------------------------------- Green's functions -- */
 enum { ORC_HE = 0, ORC_VG = 1, ORC_VG_DCT = 2 };
 
@@ -432,6 +499,178 @@ void orc_solve_direct(int N, double h, const double *T, const double *rho, const
                 const double *rrow = rho + ((size_t)jz * N + jy) * N;
                 for (int jx = 0; jx < N; ++jx) {
                     double t = Trow[abs(ix - jx)] * rrow[jx];
+                    double s = sum + t;
+                    if (fabs(sum) >= fabs(t))
+                        comp += (sum - s) + t;
+                    else
+                        comp += (t - s) + sum;
+                    sum = s;
+                }
+            }
+        out[p] = h * h * h * (sum + comp);
+    }
+}
+
+/* ---------------------------------------------------------- the field -- */
+/*
+ * Field kernel F_a[m] = -dG/dx_a at x = m h, m in [0,N]^3 (a = 0, 1, 2 for
+ * x, y, z), so that E_a = h^3 sum_j F_a[i-j] rho_j is the field E = -grad phi
+ * of Appendix B (Eq. efield) for the potential phi = G * rho of Sec. 1.  F_a is
+ * odd in m_a and even in the two other indices, so the octant fixes it.  The
+ * paper does not say how the gradient is discretised; the reading taken here
+ * differentiates each method's Green's function before sampling:
+ *   HE (Sec. 2.2): the gradient of 1/(4 pi |x|) sampled at m h,
+ *       F_a[m] = m_a / (4 pi h^2 |m|^3), and F_a[0] = 0 (odd symmetry).
+ *   VG (Sec. 2.3): the inverse transform of -i k_a G_L(k) on the (4N)^3 grid
+ *       (the gradient of the truncated kernel), with the Nyquist plane
+ *       j_a = -2N set to zero (k_a has no odd value there), scaled by
+ *       (4Nh)^-3, real part.
+ *   VG-DCT (Sec. 2.4): the same sum through the (2N+1)^3 octant: k_a G_L(k)
+ *       sampled at j in [0,2N]^3 is odd in j_a, so the 4N sum becomes a DST-I
+ *       along a and DCT-I along the others, scaled by (4Nh)^-3.
+ */
+void orc_field_kernel(int algo, int a, int N, double L, double alpha, double *F) {
+    double h = L / N;
+    int k1 = N + 1;
+    double Lt = alpha * sqrt(3.0) * L;
+    if (algo == ORC_HE) {
+        for (int z = 0; z < k1; ++z)
+            for (int y = 0; y < k1; ++y)
+                for (int x = 0; x < k1; ++x) {
+                    int m[3] = {x, y, z};
+                    double r2 = (double)x * x + (double)y * y + (double)z * z;
+                    F[((size_t)z * k1 + y) * k1 + x] =
+                        (x | y | z) ? (double)m[a] / (4.0 * ORC_PI * h * h * r2 * sqrt(r2)) : 0.0;
+                }
+    } else if (algo == ORC_VG) {
+        int n4 = 4 * N;
+        size_t tot = (size_t)n4 * n4 * n4;
+        cplx *g = (cplx *)malloc(sizeof(cplx) * tot);
+        double dk = 2.0 * ORC_PI / ((double)n4 * h);
+#pragma omp parallel for schedule(static)
+        for (long long idx = 0; idx < (long long)tot; ++idx) {
+            int s3[3] = {(int)(idx % n4), (int)((idx / n4) % n4), (int)(idx / ((long long)n4 * n4))};
+            int j[3];
+            for (int c = 0; c < 3; ++c) j[c] = s3[c] < 2 * N ? s3[c] : s3[c] - n4;
+            double kabs = dk * sqrt((double)j[0] * j[0] + (double)j[1] * j[1] + (double)j[2] * j[2]);
+            double ka = j[a] == -2 * N ? 0.0 : dk * j[a];
+            g[idx] = -I * ka * orc_green_vico_hat(kabs, Lt);
+        }
+        orc_fft3d(n4, n4, n4, g, +1);
+        double scale = 1.0 / (((double)n4 * h) * ((double)n4 * h) * ((double)n4 * h));
+        for (int z = 0; z < k1; ++z)
+            for (int y = 0; y < k1; ++y)
+                for (int x = 0; x < k1; ++x)
+                    F[((size_t)z * k1 + y) * k1 + x] = creal(g[((size_t)z * n4 + y) * n4 + x]) * scale;
+        free(g);
+    } else {
+        int M = 2 * N, n = M + 1;
+        double *g = (double *)malloc(sizeof(double) * (size_t)n * n * n);
+        double dk = 2.0 * ORC_PI / (4.0 * N * h);
+        for (int z = 0; z < n; ++z)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x) {
+                    int j[3] = {x, y, z};
+                    g[((size_t)z * n + y) * n + x] =
+                        dk * j[a] * orc_green_vico_hat(dk * sqrt((double)x * x + (double)y * y + (double)z * z), Lt);
+                }
+        orc_trig1_3d(M, N, a, g, F);
+        double scale = 1.0 / ((4.0 * N * h) * (4.0 * N * h) * (4.0 * N * h));
+        for (size_t i = 0; i < (size_t)k1 * k1 * k1; ++i) F[i] *= scale;
+        free(g);
+    }
+}
+
+/* Sign of the odd extension on the doubled grid: +1 on (0,N), -1 on (N,2N),
+ * 0 at 0 and at N (an odd sequence of period 2N vanishes there; no physical
+ * output reads index N, since |i - j| <= N-1). */
+static inline double odd_sign(int m, int N) { return m == 0 || m == N ? 0.0 : (m < N ? 1.0 : -1.0); }
+
+/* F_2 on the (2N)^3 doubled grid from the octant of a kernel odd in axis a. */
+static void field_doubled(int N, int a, const double *F, cplx *g2) {
+    int n2 = 2 * N, k1 = N + 1;
+    for (int z = 0; z < n2; ++z)
+        for (int y = 0; y < n2; ++y)
+            for (int x = 0; x < n2; ++x) {
+                int m[3] = {x, y, z};
+                g2[((size_t)z * n2 + y) * n2 + x] =
+                    odd_sign(m[a], N) * F[((size_t)fold2(z, N) * k1 + fold2(y, N)) * k1 + fold2(x, N)];
+            }
+}
+
+/*
+ * E_a = h^3 sum_j F_a[i-j] rho_j through Sec. 2.2 steps 1-5 on the full
+ * (2N)^3 complex grid with the odd field kernel in place of G: pad rho, FFT
+ * rho_2 and F_2, multiply, inverse FFT (1/(2N)^3), scale by h^3, restrict.
+ */
+void orc_solve_field_fft(int N, double h, int a, const double *F, const double *rho, double *E) {
+    int n2 = 2 * N;
+    size_t tot = (size_t)n2 * n2 * n2;
+    cplx *r2 = (cplx *)calloc(tot, sizeof(cplx));
+    cplx *g2 = (cplx *)malloc(sizeof(cplx) * tot);
+    for (int z = 0; z < N; ++z)
+        for (int y = 0; y < N; ++y)
+            for (int x = 0; x < N; ++x) r2[((size_t)z * n2 + y) * n2 + x] = rho[((size_t)z * N + y) * N + x];
+    field_doubled(N, a, F, g2);
+    orc_fft3d(n2, n2, n2, r2, -1);
+    orc_fft3d(n2, n2, n2, g2, -1);
+    for (size_t i = 0; i < tot; ++i) r2[i] *= g2[i];
+    orc_fft3d(n2, n2, n2, r2, +1);
+    double scale = h * h * h / (double)tot;
+    for (int z = 0; z < N; ++z)
+        for (int y = 0; y < N; ++y)
+            for (int x = 0; x < N; ++x)
+                E[((size_t)z * N + y) * N + x] = creal(r2[((size_t)z * n2 + y) * n2 + x]) * scale;
+    free(g2);
+    free(r2);
+}
+
+/*
+ * The field multiplier on the non-redundant octant.  DFT_{2N}{F_2} is purely
+ * imaginary (F_2 real, odd in a, even in the others); the value returned is
+ *   S_a[q] = -h^3 / (2N)^3 * Im DFT_{2N}{F_2}[q],  q in [0,N]^3,
+ * so that the solve multiplies by -i S_a[q] for q_a <= N (and by +i S_a at
+ * the mirrored index for q_a > N).  Computed through the full complex FFT.
+ */
+void orc_field_spectrum(int N, double h, int a, const double *F, double *S) {
+    int n2 = 2 * N, k1 = N + 1;
+    size_t tot = (size_t)n2 * n2 * n2;
+    cplx *g2 = (cplx *)malloc(sizeof(cplx) * tot);
+    field_doubled(N, a, F, g2);
+    orc_fft3d(n2, n2, n2, g2, -1);
+    double scale = h * h * h / (double)tot;
+    for (int z = 0; z < k1; ++z)
+        for (int y = 0; y < k1; ++y)
+            for (int x = 0; x < k1; ++x)
+                S[((size_t)z * k1 + y) * k1 + x] = -cimag(g2[((size_t)z * n2 + y) * n2 + x]) * scale;
+    free(g2);
+}
+
+/*
+ * The field's discrete convolution by its definition:
+ *   E_a[i] = h^3 sum_{j in [0,N)^3} sgn(i_a - j_a) F_a[|i - j|] rho_j
+ * at the `npts` flat output indices `pts` (all N^3 if pts == NULL), with
+ * Neumaier's compensated summation as in orc_solve_direct.
+ */
+void orc_solve_field_direct(int N, double h, int a, const double *F, const double *rho, const long long *pts,
+                            long long npts, double *out) {
+    int k1 = N + 1;
+    long long total = pts ? npts : (long long)N * N * N;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long p = 0; p < total; ++p) {
+        long long i = pts ? pts[p] : p;
+        int ix = (int)(i % N), iy = (int)((i / N) % N), iz = (int)(i / ((long long)N * N));
+        int ii[3] = {ix, iy, iz};
+        double sum = 0.0, comp = 0.0;
+        for (int jz = 0; jz < N; ++jz)
+            for (int jy = 0; jy < N; ++jy) {
+                const double *Frow = F + ((size_t)abs(iz - jz) * k1 + abs(iy - jy)) * k1;
+                const double *rrow = rho + ((size_t)jz * N + jy) * N;
+                for (int jx = 0; jx < N; ++jx) {
+                    int jj[3] = {jx, jy, jz};
+                    int d = ii[a] - jj[a];
+                    double sg = d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0);
+                    double t = sg * Frow[abs(ix - jx)] * rrow[jx];
                     double s = sum + t;
                     if (fabs(sum) >= fabs(t))
                         comp += (sum - s) + t;

@@ -5,7 +5,9 @@ transform sign, a wrong twiddle index, a dropped factor or scale, an
 off-by-one in the frequency grid or the mirror fold, a wrong window or series
 coefficient, a wrong stride, a padding bound), builds it with gcc on the CPU
 and runs the pins against it: at least one must fail.  The mistakes are made
-in a temporary copy; the oracle itself is never modified.
+in a temporary copy; the oracle itself is never modified.  The field
+functions have their own planted mistakes (a lost odd extension, a wrong
+power or sign or axis of the field kernel, a wrong DST factor) and pins.
 """
 import ctypes
 import os
@@ -43,6 +45,22 @@ MUTANTS = [
     ("direct_sum_h3", "out[p] = h * h * h * (sum + comp);", "out[p] = h * h * (sum + comp);"),
     ("padding_bound", "for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 0; x < N; ++x) r2[",
      "for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 1; x < N; ++x) r2["),
+]
+
+# planted mistakes in the field functions (caught by _field_pins)
+FIELD_MUTANTS = [
+    ("odd_extension_even", "return m == 0 || m == N ? 0.0 : (m < N ? 1.0 : -1.0);",
+     "return m == 0 || m == N ? 0.0 : (m < N ? 1.0 : 1.0);"),
+    ("he_field_power", "(double)m[a] / (4.0 * ORC_PI * h * h * r2 * sqrt(r2))", "(double)m[a] / (4.0 * ORC_PI * h * h * r2)"),
+    ("vg_field_sign", "g[idx] = -I * ka * orc_green_vico_hat(kabs, Lt);", "g[idx] = I * ka * orc_green_vico_hat(kabs, Lt);"),
+    ("vg_dct_field_axis", "dk * j[a] * orc_green_vico_hat(", "dk * j[0] * orc_green_vico_hat("),
+    ("dst_factor", "acc += 2.0 * x[j] * sin(", "acc += 1.0 * x[j] * sin("),
+    ("trig_kind_swap", "tab[e] = kind == 0 ? cos(ORC_PI * (double)e / M) : sin(ORC_PI * (double)e / M);",
+     "tab[e] = kind == 1 ? cos(ORC_PI * (double)e / M) : sin(ORC_PI * (double)e / M);"),
+    ("field_direct_sign", "double sg = d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0);", "double sg = d > 0 ? -1.0 : (d < 0 ? 1.0 : 0.0);"),
+    ("field_spectrum_sign", "S[((size_t)z * k1 + y) * k1 + x] = -cimag(", "S[((size_t)z * k1 + y) * k1 + x] = cimag("),
+    ("field_solve_scale", "double scale = h * h * h / (double)tot;\n    for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 0; x < N; ++x)\n                E[",
+     "double scale = h * h / (double)tot;\n    for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 0; x < N; ++x)\n                E["),
 ]
 
 
@@ -107,6 +125,55 @@ def _far_field_err(orc, algo, N, c=(-0.3, -0.3, -0.3), s=0.04):
     return float(np.max(np.abs(phi[far] - ex[far]) / ex[far]))
 
 
+def _field_pins(orc):
+    """Name -> passed, for a cheap set of the field pins."""
+    import scipy.fft as sf
+    from oracle import analytic as A
+    res = {}
+    r = np.random.default_rng(3)
+    x = r.standard_normal(9)
+    res["dst1_vs_scipy"] = np.allclose(orc.dst1(x)[1:8], sf.dst(x[1:8], type=1), atol=1e-12)
+    g = r.standard_normal((7, 7, 7))
+    want = sf.dct(sf.dct(g, type=1, axis=0), type=1, axis=1)
+    inner = sf.dst(want[:, :, 1:6], type=1, axis=2)
+    full = np.zeros_like(want)
+    full[:, :, 1:6] = inner
+    res["trig_vs_scipy"] = np.allclose(orc.trig1_3d(g, 0), full, atol=1e-10)
+    res["vg_two_routes"] = all(np.allclose(orc.field_kernel("vg", a, 4), orc.field_kernel("vg_dct", a, 4),
+                                           rtol=0, atol=1e-13 * np.abs(orc.field_kernel("vg", a, 4)).max())
+                               for a in range(3))
+    rho = I.random_field(5, 4)
+    ok = True
+    for algo in ("he", "vg_dct"):
+        for a in range(3):
+            F = orc.field_kernel(algo, a, 5)
+            e1, e2 = orc.solve_field_fft(F, a, rho, 0.2), orc.solve_field_direct(F, a, rho, 0.2)
+            ok = ok and np.allclose(e1, e2, rtol=0, atol=1e-12 * np.abs(e2).max())
+    res["fft_eq_direct"] = ok
+    N, h, j = 6, 1.0 / 6, (1, 4, 2)
+    z, y, x3 = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    d = [(x3 - j[0]) * h, (y - j[1]) * h, (z - j[2]) * h]
+    rr = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    imp = I.impulse(N, 1.0, j)
+    res["coulomb"] = all(np.allclose(orc.solve_field_fft(orc.field_kernel("he", a, N), a, imp, h),
+                                     (rr > 0) * d[a] / (4 * np.pi * np.where(rr > 0, rr, 1.0) ** 3), rtol=1e-10, atol=1e-10)
+                         for a in range(3))
+    E = orc.solve_field("vg_dct", I.gaussian(16, 1.0, 0.1))
+    ex = A.gaussian_field(16, 1.0, 0.1)
+    res["gaussian_vg16"] = max(np.abs(E[a] - ex[a]).max() for a in range(3)) < 1e-3 * np.abs(ex[0]).max()
+    ok = True
+    for a in range(3):
+        F = orc.field_kernel("vg_dct", a, 4)
+        Fz = F.copy()
+        idx = [slice(None)] * 3
+        idx[2 - a] = 4
+        Fz[tuple(idx)] = 0.0
+        ok = ok and np.allclose(orc.field_spectrum(F, a, 0.25), orc.trig1_3d(Fz, a) * 0.25 ** 3 / 8 ** 3,
+                                rtol=0, atol=1e-12 * np.abs(Fz).max())
+    res["spectrum_two_routes"] = ok
+    return res
+
+
 @pytest.fixture(scope="module")
 def baseline(orc):
     return _pins(orc)
@@ -116,8 +183,12 @@ def test_pins_pass_on_the_oracle(baseline):
     assert all(baseline.values()), baseline
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(orc, name, old, new):
+def test_field_pins_pass_on_the_oracle(orc):
+    res = _field_pins(orc)
+    assert all(res.values()), res
+
+
+def _run_mutant(orc, name, old, new, pins):
     with tempfile.TemporaryDirectory() as tmp:
         path = _build(name, old, new, tmp)
         saved = orc._lib
@@ -127,10 +198,23 @@ def test_planted_mistake_fails_a_pin(orc, name, old, new):
             orig_build = orc._build.build
             orc._build.build = lambda force=False: path  # load the mutant instead
             orc._load()
-            res = _pins(orc)
+            res = pins(orc)
         finally:
             orc._build.build = orig_build
             orc._lib = saved
         del mutant
+    return res
+
+
+@pytest.mark.parametrize("name,old,new", FIELD_MUTANTS, ids=[m[0] for m in FIELD_MUTANTS])
+def test_planted_field_mistake_fails_a_pin(orc, name, old, new):
+    res = _run_mutant(orc, name, old, new, _field_pins)
+    failed = [k for k, ok in res.items() if not ok]
+    assert failed, "no field pin caught the planted mistake " + name
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(orc, name, old, new):
+    res = _run_mutant(orc, name, old, new, _pins)
     failed = [k for k, ok in res.items() if not ok]
     assert failed, "no pin caught the planted mistake " + name

@@ -109,6 +109,50 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
 fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stream);
 
 /*
+ * fsp_plan_field_init -- plan-time set-up of field solves (fsp_solve_field):
+ * the field kernels F_a = -dG/dx_a (a = x, y, z) of the plan's method and
+ * their spectra, FP64, rounded to the plan's type, plus a third workspace of
+ * 2 N^2 P complex values.  E = -grad phi is the field of Appendix B (Eq.
+ * efield), the step after the solve in the paper's particle-in-cell loop.
+ *   FSP_HE:            F_a[m] = m_a / (4 pi h^2 |m|^3), F_a[0] = 0 (the
+ *                      sampled gradient of the kernel of Sec. 2.2).
+ *   FSP_VG, FSP_VG_DCT: the inverse transform of -i k_a G_L(k) (Sec. 2.3,
+ *                      Eq. green_vico), evaluated through the (2N+1)^3
+ *                      octant as a DST-I along a and DCT-I along the other
+ *                      axes (Sec. 2.4), with the Nyquist plane j_a = -2N at
+ *                      zero.  Both forms use this octant route: it equals the
+ *                      (4N)^3 transform to rounding and needs 1/64 of its
+ *                      memory.
+ * The spectrum of F_a is odd in k_a: S_a = h^3 / (2N)^3 DST_a DCT DCT (F_a);
+ * the solve multiplies by -i S_a.  Runs on `stream` and returns after it has
+ * completed; temporaries ((2N+1)^3 FP64 for the Vico-Greengard forms) are
+ * freed.  Calling it again is a no-op.  FSP_EINVAL for a spectrum-only plan
+ * (no workspace); FSP_ENOMEM when the buffers do not fit, leaving the plan
+ * usable for potential solves.
+ */
+fsp_status fsp_plan_field_init(fsp_plan *plan, fsp_stream stream);
+
+/*
+ * fsp_solve_field -- the field E = -grad phi of rho (Appendix B, Eq. efield)
+ * and optionally phi itself: E_a[i] = h^3 sum_j F_a[i - j] rho_j for
+ * a = x, y, z, each through the doubled grid like fsp_solve with the odd
+ * spectrum -i S_a in place of S.  The forward transforms of rho (P1, P2)
+ * run once; each output then takes its own P3 (z-FFT, multiply, z-IFFT, into
+ * the third workspace), P4 and P5, so one call is 2 + 3 x 3 launches (+3
+ * with phi) on `stream`, asynchronous.
+ *
+ * rho: DEVICE pointer, N^3 reals of the plan's dtype.  ex, ey, ez: DEVICE
+ * pointers, N^3 reals each, the components along x (the fastest index), y
+ * and z; phi: the same for the potential, or NULL.  All 16-byte aligned.
+ * The outputs must not overlap one another; any of them may be rho (rho is
+ * read completely before the first output is written).  Runs
+ * fsp_plan_field_init first if it has not been called (synchronously, on
+ * `stream`).  One solve per plan in flight, as for fsp_solve.
+ */
+fsp_status fsp_solve_field(fsp_plan *plan, const void *rho, void *phi, void *ex, void *ey, void *ez,
+                           fsp_stream stream);
+
+/*
  * fsp_solve_host -- the same solve on HOST arrays: copies rho host->device,
  * solves, copies phi device->host, all on `stream`, and returns after the
  * stream has completed the copy back.  rho/phi: host pointers (pinned memory

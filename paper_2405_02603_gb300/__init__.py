@@ -74,6 +74,8 @@ def lib(build_if_missing=True):
     L.fsp_fft_c2c.argtypes = [i, i, i, i, vp, vp, vp]
     L.fsp_plan_set_timing.argtypes = [vp, ctypes.POINTER(vp), i]
     L.fsp_solve_noalloc.argtypes = [i, vp, vp, vp, vp]
+    L.fsp_plan_field_init.argtypes = [vp, vp]
+    L.fsp_solve_field.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fsp_plan_uses_fast_path.argtypes = [vp]
     L.fsp_plan_uses_fast_path.restype = i
     vpp = ctypes.POINTER(vp)
@@ -104,7 +106,8 @@ def lib(build_if_missing=True):
                  "fsp_batch_inject_stall", "fsp_batch_destroy", "fsp_solve_batched"):
         getattr(L, name).restype = i
     for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
-                 "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc"):
+                 "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc", "fsp_plan_field_init",
+                 "fsp_solve_field"):
         getattr(L, name).restype = i
     _lib = L
     table = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.txt")
@@ -178,6 +181,25 @@ class Plan:
         import torch
         phi = torch.empty_like(rho)
         return self.solve_into(rho, phi, stream)
+
+    def field_init(self, stream=None):
+        """Plan-time set-up of field solves (fsp_plan_field_init)."""
+        check(lib().fsp_plan_field_init(self._p, _stream_handle(stream)), "fsp_plan_field_init")
+
+    def solve_field_into(self, rho, ex, ey, ez, phi=None, stream=None):
+        """Enqueue E = -grad phi (and phi if given) of rho: fsp_solve_field."""
+        for t in (rho, ex, ey, ez) + ((phi,) if phi is not None else ()):
+            self._check_tensor(t)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        check(lib().fsp_solve_field(self._p, ptr(rho), ptr(phi), ptr(ex), ptr(ey), ptr(ez), _stream_handle(stream)),
+              "fsp_solve_field")
+        return (ex, ey, ez) if phi is None else (ex, ey, ez, phi)
+
+    def solve_field(self, rho, with_phi=False, stream=None):
+        """(E_x, E_y, E_z), or (E_x, E_y, E_z, phi) with with_phi, as new tensors."""
+        import torch
+        outs = [torch.empty_like(rho) for _ in range(4 if with_phi else 3)]
+        return self.solve_field_into(rho, *outs[:3], phi=outs[3] if with_phi else None, stream=stream)
 
     def solve_host(self, rho_host, phi_host, stream=None):
         """Host arrays (numpy or CPU tensors, ideally pinned): copy in, solve, copy out."""

@@ -154,6 +154,55 @@ struct Temps {
     DevBuf g, a1, a2, tw;
 };
 
+// DCT-I (kind false) or DST-I (kind true) of real lines, FP64.
+cudaError_t launch_trig(bool dst, const LinesArgs &a, cudaStream_t s) {
+    return dst ? launch_lines<double, IN_REAL_ODD, OUT_REAL, M_FWD>(a, s)
+               : launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s);
+}
+
+// Separable transform of the (2N+1)^3 octant g (M = 2N samples per axis,
+// extended to 4N): DST-I along axis `odd` (0 = x, 1 = y, 2 = z; -1: none) and
+// DCT-I along the others, outputs [0,N] per axis into out ((N+1)^3), FP64.
+// This is the (4N)^3 DFT of a sequence even (or, along `odd`, odd) in every
+// axis (Sec. 2.4).  Temporaries in tmp.a1, tmp.a2, tmp.tw.
+fsp_status enqueue_octant_transform(int N, int odd, const double *g, double *out, cudaStream_t s, Temps &tmp) {
+    const int k1 = N + 1, M = 2 * N, nm = M + 1, n = 2 * M;
+    fsp_status st;
+    TileCfg cr, cc;
+    if (!make_cfg(n, n, sizeof(double2), 3, cr) || !make_cfg(n, n, sizeof(double2), 3, cc)) return FSP_EUNSUPPORTED;
+    if ((st = alloc_or_nomem(tmp.a1, sizeof(double) * (size_t)nm * nm * k1)) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(tmp.a2, sizeof(double) * (size_t)nm * k1 * k1)) != FSP_OK) return st;
+    if ((st = roots_f64(tmp.tw, n, s)) != FSP_OK) return st;
+    LinesArgs a{};
+    a.tw = tmp.tw.p;
+    a.st = cr.st;
+    a.tpl = cr.tpl;
+    a.lgL = cr.lgL;
+    // x: rows of M+1 reals -> rows of N+1
+    a.in = g;
+    a.out = tmp.a1.p;
+    a.in_pos = 1, a.in_line = nm, a.in_batch = 0;
+    a.out_pos = 1, a.out_line = k1, a.out_batch = 0;
+    a.n_out = k1, a.nlines = nm * nm, a.nbatch = 1;
+    FSP_TRY_CUDA(launch_trig(odd == 0, a, s));
+    // y: columns (x in [0,N]) of a1[z][y][x]
+    a.tpl = cc.tpl, a.lgL = cc.lgL;
+    a.in = tmp.a1.p;
+    a.out = tmp.a2.p;
+    a.in_pos = k1, a.in_line = 1, a.in_batch = (long long)nm * k1;
+    a.out_pos = k1, a.out_line = 1, a.out_batch = (long long)k1 * k1;
+    a.n_out = k1, a.nlines = k1, a.nbatch = nm;
+    FSP_TRY_CUDA(launch_trig(odd == 1, a, s));
+    // z: columns of a2[z][y][x], batch y
+    a.in = tmp.a2.p;
+    a.out = out;
+    a.in_pos = (long long)k1 * k1, a.in_line = 1, a.in_batch = k1;
+    a.out_pos = (long long)k1 * k1, a.out_line = 1, a.out_batch = k1;
+    a.n_out = k1, a.nlines = k1, a.nbatch = k1;
+    FSP_TRY_CUDA(launch_trig(odd == 2, a, s));
+    return FSP_OK;
+}
+
 fsp_status enqueue_kernel_T(int N, double L, fsp_algo algo, double *t_dev, cudaStream_t s, Temps &tmp) {
     const double h = L / N;
     const int k1 = N + 1;
@@ -165,41 +214,10 @@ fsp_status enqueue_kernel_T(int N, double L, fsp_algo algo, double *t_dev, cudaS
     if (algo == FSP_VG_DCT) {
         // Sec. 2.4: G_L on [0,2N]^3, DCT-I per axis (M = 2N, even extension to
         // 4N), keeping outputs [0,N] of each axis, then (4Nh)^-3.
-        const int M = 2 * N, nm = M + 1, n = 2 * M;
-        TileCfg cr, cc;
-        if (!make_cfg(n, n, sizeof(double2), 3, cr) || !make_cfg(n, n, sizeof(double2), 3, cc)) return FSP_EUNSUPPORTED;
+        const int nm = 2 * N + 1;
         if ((st = alloc_or_nomem(tmp.g, sizeof(double) * (size_t)nm * nm * nm)) != FSP_OK) return st;
-        if ((st = alloc_or_nomem(tmp.a1, sizeof(double) * (size_t)nm * nm * k1)) != FSP_OK) return st;
-        if ((st = alloc_or_nomem(tmp.a2, sizeof(double) * (size_t)nm * k1 * k1)) != FSP_OK) return st;
-        if ((st = roots_f64(tmp.tw, n, s)) != FSP_OK) return st;
         FSP_TRY_CUDA(launch_vg_sample_octant((double *)tmp.g.p, N, h, Lt, s));
-        LinesArgs a{};
-        a.tw = tmp.tw.p;
-        a.st = cr.st;
-        a.tpl = cr.tpl;
-        a.lgL = cr.lgL;
-        // x: rows of M+1 reals -> rows of N+1
-        a.in = tmp.g.p;
-        a.out = tmp.a1.p;
-        a.in_pos = 1, a.in_line = nm, a.in_batch = 0;
-        a.out_pos = 1, a.out_line = k1, a.out_batch = 0;
-        a.n_out = k1, a.nlines = nm * nm, a.nbatch = 1;
-        FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
-        // y: columns (x in [0,N]) of a1[z][y][x]
-        a.tpl = cc.tpl, a.lgL = cc.lgL;
-        a.in = tmp.a1.p;
-        a.out = tmp.a2.p;
-        a.in_pos = k1, a.in_line = 1, a.in_batch = (long long)nm * k1;
-        a.out_pos = k1, a.out_line = 1, a.out_batch = (long long)k1 * k1;
-        a.n_out = k1, a.nlines = k1, a.nbatch = nm;
-        FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
-        // z: columns of a2[z][y][x], batch y
-        a.in = tmp.a2.p;
-        a.out = t_dev;
-        a.in_pos = (long long)k1 * k1, a.in_line = 1, a.in_batch = k1;
-        a.out_pos = (long long)k1 * k1, a.out_line = 1, a.out_batch = k1;
-        a.n_out = k1, a.nlines = k1, a.nbatch = k1;
-        FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+        if ((st = enqueue_octant_transform(N, -1, (double *)tmp.g.p, t_dev, s, tmp)) != FSP_OK) return st;
         return cuda_status(launch_scale(t_dev, (long long)k1 * k1 * k1, scale, s));
     }
     // FSP_VG, Sec. 2.3: G_L on the (4N)^3 grid, unnormalised inverse DFT per
@@ -235,8 +253,10 @@ fsp_status enqueue_kernel_T(int N, double L, fsp_algo algo, double *t_dev, cudaS
 }
 
 // Spectrum of the mirrored kernel: DCT-I of length N+1 per axis on T in place
-// (the 2N DFT of a real sequence even about 0 and N), FP64.
-fsp_status enqueue_dct_spectrum(int N, double *t_dev, cudaStream_t s, DevBuf &tw) {
+// (the 2N DFT of a real sequence even about 0 and N), FP64.  For a field
+// kernel odd in axis `odd` (0 = x, 1 = y, 2 = z) that axis takes the DST-I
+// instead: the 2N DFT of the odd extension is -i times the result.
+fsp_status enqueue_trig_spectrum(int N, int odd, double *t_dev, cudaStream_t s, DevBuf &tw) {
     const int k1 = N + 1, n = 2 * N;
     TileCfg c;
     if (!make_cfg(n, n, sizeof(double2), 3, c)) return FSP_EUNSUPPORTED;
@@ -249,15 +269,39 @@ fsp_status enqueue_dct_spectrum(int N, double *t_dev, cudaStream_t s, DevBuf &tw
     // x: rows
     a.in_pos = a.out_pos = 1, a.in_line = a.out_line = k1, a.in_batch = a.out_batch = 0;
     a.nlines = k1 * k1, a.nbatch = 1;
-    FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+    FSP_TRY_CUDA(launch_trig(odd == 0, a, s));
     // y: columns, batch z
     a.in_pos = a.out_pos = k1, a.in_line = a.out_line = 1, a.in_batch = a.out_batch = (long long)k1 * k1;
     a.nlines = k1, a.nbatch = k1;
-    FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+    FSP_TRY_CUDA(launch_trig(odd == 1, a, s));
     // z: columns, batch y
     a.in_pos = a.out_pos = (long long)k1 * k1, a.in_batch = a.out_batch = k1;
-    FSP_TRY_CUDA((launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s)));
+    FSP_TRY_CUDA(launch_trig(odd == 2, a, s));
     return FSP_OK;
+}
+
+fsp_status enqueue_dct_spectrum(int N, double *t_dev, cudaStream_t s, DevBuf &tw) {
+    return enqueue_trig_spectrum(N, -1, t_dev, s, tw);
+}
+
+// Field kernel F_a[m] = -dG/dx_a (m h), m in [0,N]^3, into f_dev (FP64), for
+// E = -grad phi (Appendix B, Eq. efield).  Hockney-Eastwood: the sampled
+// gradient of 1/(4 pi |x|), zero at the origin.  Vico-Greengard (both forms):
+// the inverse transform of -i k_a G_L (Sec. 2.3) through the (2N+1)^3 octant,
+// where k_a G_L is odd in j_a: DST-I along a, DCT-I along the others, times
+// (4Nh)^-3 (the octant form of the (4N)^3 sum with its Nyquist plane j_a = -2N
+// at zero).
+fsp_status enqueue_field_kernel(int N, double L, fsp_algo algo, int axis, double *f_dev, cudaStream_t s, Temps &tmp) {
+    const double h = L / N;
+    const int k1 = N + 1, nm = 2 * N + 1;
+    if (algo == FSP_HE) return cuda_status(launch_he_F(f_dev, N, h, axis, s));
+    const double Lt = kAlpha * std::sqrt(3.0) * L;
+    fsp_status st;
+    if ((st = alloc_or_nomem(tmp.g, sizeof(double) * (size_t)nm * nm * nm)) != FSP_OK) return st;
+    FSP_TRY_CUDA(launch_vg_sample_octant_grad((double *)tmp.g.p, N, h, Lt, axis, s));
+    if ((st = enqueue_octant_transform(N, axis, (double *)tmp.g.p, f_dev, s, tmp)) != FSP_OK) return st;
+    const double scale = 1.0 / ((4.0 * N * h) * (4.0 * N * h) * (4.0 * N * h));
+    return cuda_status(launch_scale(f_dev, (long long)k1 * k1 * k1, scale, s));
 }
 
 fsp_status validate_size(int N, double L, fsp_algo algo) {
@@ -289,6 +333,9 @@ struct fsp_plan {
     cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
     TileCfg row, col;
     bool fast = false;  // specialised power-of-two kernels (fast.cuh) serve this N
+    // field solves (fsp_plan_field_init): the spectra of F_x, F_y, F_z and the
+    // third workspace the out-of-place P3 of each component writes
+    void *SF[3] = {}, *W3 = nullptr;
     cudaEvent_t ev[6] = {};
     bool timing = false;
     size_t bytes = 0;
@@ -304,7 +351,7 @@ bool plan_live(const fsp_plan *p) {
 
 void plan_free(fsp_plan *p) {
     for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi, p->pipe_rho[0], p->pipe_rho[1],
-                    p->pipe_phi[0], p->pipe_phi[1]})
+                    p->pipe_phi[0], p->pipe_phi[1], p->SF[0], p->SF[1], p->SF[2], p->W3})
         if (q) cudaFree(q);
     for (cudaStream_t q : {p->pipe_h2d, p->pipe_d2h})
         if (q) cudaStreamDestroy(q);
@@ -386,6 +433,88 @@ cudaError_t enqueue_solve_generic(const fsp_plan *p, const void *rho, void *phi,
     r.x = phi;
     if ((e = launch_c2r_rows<T>(r, s)) != cudaSuccess) return e;
     return mark(5);
+}
+
+// The field E = -grad phi (and phi, when out[3] is set): P1 and P2 once, then
+// per output P3 (W2 -> W3 with that output's spectrum), P4 (W3 -> W1), P5
+// (W1 -> output).  out[0..2] = E_x, E_y, E_z, out[3] = phi or null.  The odd
+// axis of component a is the line (k_x), the batch (k_y) or the position (z)
+// of the P3 pass.
+constexpr int kP3Odd[3] = {3, 2, 1};
+
+template <typename T>
+cudaError_t enqueue_field_fast(const fsp_plan *p, const void *rho, void *const out[4], cudaStream_t s) {
+    const int N = p->N;
+    const long long P = p->P;
+    cudaError_t e;
+    fast::RowArgs r{};
+    r.x = rho, r.c = p->W1, r.x_row = N, r.c_row = P, r.nrows = N * N, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    if ((e = fast::p1<T>(N, r, s)) != cudaSuccess) return e;
+    fast::ColArgs a{};
+    a.tw = p->tw_2n, a.nlines = N + 1;
+    a.in = p->W1, a.out = p->W2;
+    a.in_pos = P, a.in_batch = (long long)N * P, a.out_pos = P, a.out_batch = 2LL * N * P;
+    if ((e = fast::p2<T>(N, a, N, s)) != cudaSuccess) return e;
+    for (int c = 3; c >= 0; --c) {
+        if (!out[c]) continue;
+        fast::ColArgs b = a;
+        b.in = p->W2, b.out = p->W3;
+        b.in_pos = b.out_pos = 2LL * N * P, b.in_batch = b.out_batch = P;
+        b.S = c == 3 ? p->S : p->SF[c], b.s_pos = (long long)(N + 1) * P, b.s_batch = P, b.half = N;
+        b.odd = c == 3 ? 0 : kP3Odd[c];
+        if ((e = fast::p3<T>(N, b, 2 * N, s)) != cudaSuccess) return e;
+        b.in = p->W3, b.out = p->W1, b.odd = 0;
+        b.in_pos = P, b.in_batch = 2LL * N * P, b.out_pos = P, b.out_batch = (long long)N * P;
+        if ((e = fast::p4<T>(N, b, N, s)) != cudaSuccess) return e;
+        r.x = out[c];
+        if ((e = fast::p5<T>(N, r, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t enqueue_field_generic(const fsp_plan *p, const void *rho, void *const out[4], cudaStream_t s) {
+    const int N = p->N;
+    const long long P = p->P;
+    cudaError_t e;
+    RowsArgs r{};
+    r.x = rho, r.c = p->W1, r.x_row = N, r.c_row = P, r.N = N, r.nrows = N * N;
+    r.lgL = p->row.lgL, r.tpl = p->row.tpl, r.st = p->row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    if ((e = launch_r2c_rows<T>(r, s)) != cudaSuccess) return e;
+    LinesArgs a{};
+    a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_2n;
+    a.in = p->W1, a.out = p->W2;
+    a.in_pos = P, a.in_line = 1, a.in_batch = (long long)N * P;
+    a.out_pos = P, a.out_line = 1, a.out_batch = 2LL * N * P;
+    a.n_in = N, a.n_out = 2 * N, a.nlines = N + 1, a.nbatch = N;
+    if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD>(a, s)) != cudaSuccess) return e;
+    for (int c = 3; c >= 0; --c) {
+        if (!out[c]) continue;
+        LinesArgs b = a;
+        b.in = p->W2, b.out = p->W3;
+        b.in_pos = b.out_pos = 2LL * N * P, b.in_batch = b.out_batch = P;
+        b.n_in = N, b.n_out = N, b.nbatch = 2 * N;
+        b.S = c == 3 ? p->S : p->SF[c], b.s_pos = (long long)(N + 1) * P, b.s_batch = P, b.half = N;
+        b.odd = c == 3 ? 0 : kP3Odd[c];
+        if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD_MUL_INV>(b, s)) != cudaSuccess) return e;
+        b.in = p->W3, b.out = p->W1, b.odd = 0;
+        b.in_pos = P, b.in_batch = 2LL * N * P;
+        b.out_pos = P, b.out_batch = (long long)N * P;
+        b.n_in = 2 * N, b.n_out = N, b.nbatch = N;
+        if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_INV>(b, s)) != cudaSuccess) return e;
+        r.x = out[c];
+        if ((e = launch_c2r_rows<T>(r, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_field(const fsp_plan *p, const void *rho, void *const out[4], cudaStream_t s) {
+    if (p->dtype == FSP_F64_DF) return enqueue_field_fast<df>(p, rho, out, s);
+    if (p->fast)
+        return p->dtype == FSP_F64 ? enqueue_field_fast<double>(p, rho, out, s)
+                                   : enqueue_field_fast<float>(p, rho, out, s);
+    return p->dtype == FSP_F64 ? enqueue_field_generic<double>(p, rho, out, s)
+                               : enqueue_field_generic<float>(p, rho, out, s);
 }
 
 // One solve of plan p with the given workspace (W1: N*N*P, W2: 2*N*N*P complex).
@@ -525,6 +654,68 @@ fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stre
     if (!plan->W1) return FSP_EINVAL;  // a spectrum-only plan (server cache) has no workspace
     const cudaError_t e = enqueue_solve_ws(plan, rho, phi, plan->W1, plan->W2, s);
     return cuda_status(e);
+}
+
+fsp_status fsp_plan_field_init(fsp_plan *plan, fsp_stream stream) {
+    if (!plan_live(plan)) return FSP_EINVAL;
+    if (!plan->W1) return FSP_EINVAL;
+    if (plan->W3) return FSP_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    if (dev != plan->device) return FSP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int N = plan->N;
+    const size_t k1 = N + 1;
+    const size_t sbytes = k1 * k1 * plan->P * plan->rsize;
+    const size_t w2 = 2 * (size_t)N * N * plan->P * 2 * plan->rsize;
+    DevBuf bs[3], bw;
+    fsp_status st;
+    for (auto &b : bs)
+        if ((st = alloc_or_nomem(b, sbytes)) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(bw, w2)) != FSP_OK) return st;
+    const double hh = plan->h;
+    const double scale = hh * hh * hh / ((2.0 * N) * (2.0 * N) * (2.0 * N));
+    for (int axis = 0; axis < 3; ++axis) {
+        // plan-time field spectrum S_a = h^3 / (2N)^3 * DST/DCT of F_a, FP64,
+        // rounded to the plan's type; each component's temporaries live
+        // until its work has finished
+        Temps tmp;
+        DevBuf Fd, tw;
+        if ((st = alloc_or_nomem(Fd, sizeof(double) * k1 * k1 * k1)) != FSP_OK) return st;
+        if ((st = enqueue_field_kernel(N, plan->L, plan->algo, axis, (double *)Fd.p, s, tmp)) != FSP_OK) {
+            cudaStreamSynchronize(s);
+            return st;
+        }
+        if ((st = enqueue_trig_spectrum(N, axis, (double *)Fd.p, s, tw)) != FSP_OK) {
+            cudaStreamSynchronize(s);
+            return st;
+        }
+        cudaError_t e = plan->dtype == FSP_F64 ? launch_store_S<double>((double *)Fd.p, bs[axis].p, N, plan->P, scale, s)
+                        : plan->dtype == FSP_F64_DF
+                            ? launch_store_S<df>((double *)Fd.p, bs[axis].p, N, plan->P, scale, s)
+                            : launch_store_S<float>((double *)Fd.p, bs[axis].p, N, plan->P, scale, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess || e != cudaSuccess) return FSP_ECUDA;
+    }
+    for (int axis = 0; axis < 3; ++axis) plan->SF[axis] = bs[axis].release();
+    plan->W3 = bw.release();
+    plan->bytes += 3 * sbytes + w2;
+    plan->precompute_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return FSP_OK;
+}
+
+fsp_status fsp_solve_field(fsp_plan *plan, const void *rho, void *phi, void *ex, void *ey, void *ez,
+                           fsp_stream stream) {
+    if (!plan_live(plan)) return FSP_EINVAL;
+    if (!rho || !ex || !ey || !ez || !aligned16(rho) || !aligned16(ex) || !aligned16(ey) || !aligned16(ez))
+        return FSP_EINVAL;
+    if (phi && !aligned16(phi)) return FSP_EINVAL;
+    if (ex == ey || ey == ez || ex == ez || (phi && (phi == ex || phi == ey || phi == ez))) return FSP_EINVAL;
+    if (!plan->W1) return FSP_EINVAL;
+    fsp_status st = fsp_plan_field_init(plan, stream);
+    if (st != FSP_OK) return st;
+    void *const out[4] = {ex, ey, ez, phi};
+    return cuda_status(enqueue_field(plan, rho, out, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 fsp_status fsp_solve_host(fsp_plan *plan, const void *rho_host, void *phi_host, fsp_stream stream) {

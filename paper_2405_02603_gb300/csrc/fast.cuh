@@ -334,23 +334,38 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         const int fy = (int)bt <= N ? (int)bt : n - (int)bt;
         const T *Sy = reinterpret_cast<const T *>(a.S) + (long long)fy * G::S_BATCH + line;
         const T *S_up = Sy + (long long)t * G::S_POS, *S_dn = Sy - (long long)t * G::S_POS;
+        // a field component's odd spectrum: multiplier -i S, negated past the
+        // fold in z (per register, mostly known at compile time) or in k_y
+        const int odd = a.odd;
+        const T sy = odd == 2 && (int)bt > N ? T(-1) : T(1);
         StaticFor<0, V / RL>::run([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             StaticFor<0, RL>::run([&](auto rc) {
                 constexpr int r = decltype(rc)::value;
                 constexpr int c = k * TPL + r * (n / RL);
                 T s;
+                bool upper;  // z = t + c > N
                 if constexpr (c + TPL - 1 <= N) {
                     s = ok ? S_up[(long long)c * G::S_POS] : T(0);
+                    upper = false;
                 } else if constexpr (c > N) {
                     s = ok ? S_dn[(long long)(n - c) * G::S_POS] : T(0);
+                    upper = true;
                 } else {
                     const int p = t + c;
                     const int fz = p <= N ? p : n - p;
                     s = ok ? Sy[(long long)fz * G::S_POS] : T(0);
+                    upper = p > N;
                 }
-                v[k * RL + r].x *= s;
-                v[k * RL + r].y *= s;
+                if (odd == 0) {
+                    v[k * RL + r].x *= s;
+                    v[k * RL + r].y *= s;
+                } else {
+                    if (odd == 1 && upper) s = -s;
+                    s *= sy;
+                    const C w = v[k * RL + r];
+                    v[k * RL + r] = C{s * w.y, -(s * w.x)};
+                }
             });
         });
         // inverse, radix schedule reversed: its stage 0 is the forward's last

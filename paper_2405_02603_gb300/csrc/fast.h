@@ -16,6 +16,10 @@ struct ColArgs {
     const void *S;   // P3: real spectrum S[fold(p)*s_pos + fold(b)*s_batch + c]
     long long s_pos, s_batch;
     int half;        // N
+    // P3: 0 for the potential's even spectrum; 1, 2, 3 for a field
+    // component's spectrum, odd in z (the position), k_y (the batch) or k_x
+    // (the line): the multiplier is -i S[fold], negated where z or k_y > N
+    int odd;
 };
 
 // Row pass: rows of N reals (x, stride x_row) <-> rows of N+1 complex (c,

@@ -1,7 +1,8 @@
 // greens.cu -- plan-time sampling kernels of the Green's functions (always
 // FP64): the Hockney-Eastwood kernel (Sec. 2.2 step 3), the Vico-Greengard
 // truncated spectral kernel sampled on the (4N)^3 frequency grid (Sec. 2.3,
-// Eq. green_vico) and on its (2N+1)^3 non-negative octant (Sec. 2.4), plus
+// Eq. green_vico) and on its (2N+1)^3 non-negative octant (Sec. 2.4), the
+// same two for the field kernel F = -grad G (Appendix B, Eq. efield), plus
 // scaling and the rounding of the spectrum to the solve's type.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -67,6 +68,31 @@ __global__ void k_vg_sample_full(double2 *g, int n4, double dk, double Lt) {
     }
 }
 
+// Field kernel of Hockney-Eastwood: F_a[m] = m_a / (4 pi h^2 |m|^3), F_a[0] = 0,
+// m in [0,N]^3, x fastest (a = 0, 1, 2 for x, y, z).
+__global__ void k_he_F(double *F, int N, double h, int a) {
+    const int k1 = N + 1;
+    const long long tot = (long long)k1 * k1 * k1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % k1), y = (int)((i / k1) % k1), z = (int)(i / ((long long)k1 * k1));
+        const int ma = a == 0 ? x : (a == 1 ? y : z);
+        const double r2 = (double)x * x + (double)y * y + (double)z * z;
+        F[i] = (x | y | z) ? inv4pi() * (double)ma / (h * h * r2 * sqrt(r2)) : 0.0;
+    }
+}
+
+// g[j] = dk j_a G_L(dk |j|) for j in [0,M]^3 (M = 2N): the octant of k_a G_L,
+// odd in j_a, whose DST-I (axis a) / DCT-I (others) gives the field kernel.
+__global__ void k_vg_sample_octant_grad(double *g, int M, double dk, double Lt, int a) {
+    const int n = M + 1;
+    const long long tot = (long long)n * n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+        const int ja = a == 0 ? x : (a == 1 ? y : z);
+        g[i] = dk * (double)ja * green_vico_hat(dk * sqrt((double)x * x + (double)y * y + (double)z * z), Lt);
+    }
+}
+
 __global__ void k_scale(double *a, long long n, double s) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] *= s;
@@ -119,6 +145,20 @@ cudaError_t launch_vg_sample_full(void *g, int N, double h, double Lt, cudaStrea
     const long long tot = (long long)n4 * n4 * n4;
     const double dk = 6.283185307179586476925286766559 / (4.0 * N * h);
     k_vg_sample_full<<<grid_for(tot), 256, 0, s>>>(reinterpret_cast<double2 *>(g), n4, dk, Lt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_he_F(double *F, int N, double h, int a, cudaStream_t s) {
+    const long long tot = (long long)(N + 1) * (N + 1) * (N + 1);
+    k_he_F<<<grid_for(tot), 256, 0, s>>>(F, N, h, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vg_sample_octant_grad(double *g, int N, double h, double Lt, int a, cudaStream_t s) {
+    const int M = 2 * N;
+    const long long tot = (long long)(M + 1) * (M + 1) * (M + 1);
+    const double dk = 6.283185307179586476925286766559 / (4.0 * N * h);
+    k_vg_sample_octant_grad<<<grid_for(tot), 256, 0, s>>>(g, M, dk, Lt, a);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,8 @@ namespace fsp {
 cudaError_t launch_he_T(double *T, int N, double h, cudaStream_t s);
 cudaError_t launch_vg_sample_octant(double *g, int N, double h, double Lt, cudaStream_t s);
 cudaError_t launch_vg_sample_full(void *g, int N, double h, double Lt, cudaStream_t s);
+cudaError_t launch_he_F(double *F, int N, double h, int a, cudaStream_t s);
+cudaError_t launch_vg_sample_octant_grad(double *g, int N, double h, double Lt, int a, cudaStream_t s);
 cudaError_t launch_scale(double *a, long long n, double sc, cudaStream_t s);
 template <typename T> cudaError_t launch_store_S(const double *Sd, void *S, int N, int P, double scale, cudaStream_t s);
 template <typename T> cudaError_t launch_load_S(const void *S, double *Sd, int N, int P, cudaStream_t s);

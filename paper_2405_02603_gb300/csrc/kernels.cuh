@@ -9,7 +9,7 @@
 
 namespace fsp {
 
-enum InKind { IN_CPLX = 0, IN_REAL_EVEN = 1 };
+enum InKind { IN_CPLX = 0, IN_REAL_EVEN = 1, IN_REAL_ODD = 2 };
 enum OutKind { OUT_CPLX = 0, OUT_REAL = 1 };
 enum Mode { M_FWD = 0, M_INV = 1, M_FWD_MUL_INV = 2 };
 
@@ -23,7 +23,9 @@ struct LinesArgs {
     long long in_pos, in_line, in_batch;
     long long out_pos, out_line, out_batch;
     int n_in;    // IN_CPLX: positions loaded, the rest of the n are zero (padding);
-                 // IN_REAL_EVEN: M+1 real samples, even-extended to n = 2M (DCT-I)
+                 // IN_REAL_EVEN: M+1 real samples, even-extended to n = 2M (DCT-I);
+                 // IN_REAL_ODD: the M-1 interior samples, i times their odd
+                 // extension to n = 2M, whose DFT is real: the DST-I
     int n_out;   // positions stored (0..n_out-1): the crop
     int nlines;  // valid lines per batch
     int nbatch;
@@ -36,6 +38,10 @@ struct LinesArgs {
     const void *S;
     long long s_pos, s_batch;
     int half;
+    // 0: S is even in every index (the potential).  1, 2, 3: S holds a
+    // spectrum odd in the position, batch or line index (a field component):
+    // the multiplier is -i S[fold], negated where that index exceeds half.
+    int odd;
 };
 
 // Real rows <-> half spectra of their zero-padded length-2N extension, through

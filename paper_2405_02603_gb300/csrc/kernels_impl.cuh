@@ -54,7 +54,9 @@ __device__ __forceinline__ void lines_tile(const LinesArgs &a, int bx, long long
         for (int idx = tid; idx < zc; idx += nth) buf[(a.n_in + (idx >> a.lgL)) * ld + (idx & lmask)] = C{T(0), T(0)};
     } else {
         // DCT-I through the DFT of the even extension: y[j] = x[j] for j <= M,
-        // y[2M - j] = x[j] for 0 < j < M.
+        // y[2M - j] = x[j] for 0 < j < M.  DST-I through the DFT of
+        // y[j] = i x[j], y[2M - j] = -i x[j] for 0 < j < M, y[0] = y[M] = 0,
+        // which is 2 sum_j x[j] sin(pi j k / M), real.
         const T *in = reinterpret_cast<const T *>(a.in) + b * a.in_batch;
         const int M = n >> 1, np = M + 1, cnt = L * np;
         const bool col = (a.in_line == 1);
@@ -69,8 +71,14 @@ __device__ __forceinline__ void lines_tile(const LinesArgs &a, int bx, long long
             }
             T x = T(0);
             if (line0 + l < a.nlines) x = ldw<COH>(in + ((long long)(line0 + l) * a.in_line + (long long)p * a.in_pos));
-            buf[p * ld + l] = C{x, T(0)};
-            if (p > 0 && p < M) buf[(n - p) * ld + l] = C{x, T(0)};
+            const bool inner = p > 0 && p < M;
+            if (IN == IN_REAL_EVEN) {
+                buf[p * ld + l] = C{x, T(0)};
+                if (inner) buf[(n - p) * ld + l] = C{x, T(0)};
+            } else {
+                buf[p * ld + l] = C{T(0), inner ? x : T(0)};
+                if (inner) buf[(n - p) * ld + l] = C{T(0), -x};
+            }
         }
     }
     __syncthreads();
@@ -88,14 +96,23 @@ __device__ __forceinline__ void lines_tile(const LinesArgs &a, int bx, long long
         const int h2 = 2 * a.half;
         const int fy = (int)b <= a.half ? (int)b : h2 - (int)b;
         const int cnt = L * n;
+        const int odd = a.odd;
+        const T sb = odd == 2 && (int)b > a.half ? T(-1) : T(1);
         for (int idx = tid; idx < cnt; idx += nth) {
             const int ll = idx & lmask, p = idx >> a.lgL;
             if (line0 + ll < a.nlines) {
                 const int fz = p <= a.half ? p : h2 - p;
-                const T s = S[(long long)fz * a.s_pos + (long long)fy * a.s_batch + line0 + ll];
+                T s = S[(long long)fz * a.s_pos + (long long)fy * a.s_batch + line0 + ll];
                 C v = buf[p * ld + ll];
-                v.x *= s;
-                v.y *= s;
+                if (odd == 0) {
+                    v.x *= s;
+                    v.y *= s;
+                } else {
+                    // -i s v; the line index (k_x <= half) never flips the sign
+                    if (odd == 1 && p > a.half) s = -s;
+                    s *= sb;
+                    v = C{s * v.y, -(s * v.x)};
+                }
                 buf[p * ld + ll] = v;
             }
         }

@@ -58,6 +58,10 @@ def test_unknown_plan_is_rejected(L):
     assert L.fsp_plan_precompute_ms(fake) < 0
     assert L.fsp_plan_spectrum(fake, fake) == 1
     assert L.fsp_plan_sync(fake, None) == 1
+    assert L.fsp_plan_field_init(fake, None) == 1
+    assert L.fsp_plan_field_init(None, None) == 1
+    assert L.fsp_solve_field(fake, fake, None, fake, fake, fake, None) == 1
+    assert L.fsp_solve_field(None, fake, None, fake, fake, fake, None) == 1
 
 
 def test_fft_and_kernel_validation(L):

@@ -250,6 +250,55 @@ def time_leg(fsp, plan, srcs, dsts, K, W, world, sampler=None):
     return {"total_ms": total_ms, "per_pass": per_pass, "per_step": per_step, "clocks": clocks}
 
 
+def field_bytes(N, c, r):
+    """Algorithmic HBM bytes of one field solve (E_x, E_y, E_z, no phi): P1
+    and P2 once, then P3 (same traffic out of place, S_a in place of S), P4
+    and P5 per component."""
+    pb = pass_bytes(N, c, r)
+    return pb[0] + pb[1] + 3 * (pb[2] + pb[3] + pb[4])
+
+
+def field_leg(fsp, N, L, algo, K, W, world):
+    """K timed FP32-mixed field solves (E = -grad phi, three components) of
+    rotating sources after W warm-ups; whole-solve CUDA-event times."""
+    import torch
+    plan = fsp.Plan(N, L, algo, "f32")
+    plan.field_init()
+    srcs, _, _ = make_sources(N, "f32")
+    outs = [[torch.empty_like(srcs[0]) for _ in range(3)] for _ in range(NSRC)]
+    stream = torch.cuda.current_stream()
+    for i in range(W):
+        plan.solve_field_into(srcs[i % NSRC], *outs[i % NSRC])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    for e in ev:
+        e.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    for i in range(K):
+        ev[i].record(stream)
+        plan.solve_field_into(srcs[i % NSRC], *outs[i % NSRC])
+    ev[K].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    per = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(K)])
+    total = ev[0].elapsed_time(ev[K])
+    value, tmax = replica_value(K, total, world)
+    t = tmax / K
+    fb = field_bytes(N, 8, 4)
+    out = {"value": round(value, 2), "unit": "field solves/s (E_x, E_y, E_z)", "steps": K,
+           "ms_per_step": round(t, 4), "p50_ms": round(float(np.percentile(per, 50)), 4),
+           "p99_ms": round(float(np.percentile(per, 99)), 4),
+           "roofline": {"bound": "hbm", "kernel": "whole field solve (P1, P2, 3 x (P3, P4, P5): 11 launches)",
+                        "achieved": round(fb / (t * 1e-3) / 1e9, 1), "unit": "GB/s",
+                        "algorithmic_bytes": fb},
+           "precompute_ms": round(plan.precompute_ms, 1), "plan_bytes": plan.bytes, "gpu_launches": 11 * K,
+           "dtype": "f32", "config": {"N": N, "L": L, "algo": algo}}
+    plan.close()
+    del srcs, outs
+    torch.cuda.empty_cache()
+    return out
+
+
 def roofline(N, c, r, leg, dtype, hbm, hbm_kind):
     pb = pass_bytes(N, c, r)
     share = leg["per_pass"].sum(axis=0)
@@ -539,6 +588,9 @@ def main():
                       "roofline": roofline(N, 16, 8, fdf, "f64df", hbm, hbm_kind),
                       "arithmetic": "double-float (float pairs) on the FP32 pipes, double arrays in and out",
                       "gpu_launches": 5 * fdf["K"]}
+    out["field"] = field_leg(fsp, N, L, args.algo, max(10, K // 4), W, world)
+    out["field"]["roofline"].update({"peak": hbm, "frac": round(out["field"]["roofline"]["achieved"] / hbm, 4),
+                                     "peak_kind": hbm_kind + " copy bandwidth"})
     if not args.no_systems:
         out["batched"] = {"f32": batch_leg(fsp, "f32"), "f64": batch_leg(fsp, "f64")}
         out["serving"] = serving_leg(fsp)

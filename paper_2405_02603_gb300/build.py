@@ -63,7 +63,7 @@ def build(force=False, verbose=False, extra=None):
     if verbose:
         extra += ["-Xptxas", "-v"]
     srcs = sources()
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(max(8, os.cpu_count() or 8), len(srcs))) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), srcs))
     failed = [r for r in results if r[2] != 0]
     for src, _, rc, log in results:

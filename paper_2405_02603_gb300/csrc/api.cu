@@ -462,7 +462,7 @@ cudaError_t enqueue_field_fast(const fsp_plan *p, const void *rho, void *const o
         b.in_pos = b.out_pos = 2LL * N * P, b.in_batch = b.out_batch = P;
         b.S = c == 3 ? p->S : p->SF[c], b.s_pos = (long long)(N + 1) * P, b.s_batch = P, b.half = N;
         b.odd = c == 3 ? 0 : kP3Odd[c];
-        if ((e = fast::p3<T>(N, b, 2 * N, s)) != cudaSuccess) return e;
+        if ((e = c == 3 ? fast::p3<T>(N, b, 2 * N, s) : fast::p3_odd<T>(N, b, 2 * N, s)) != cudaSuccess) return e;
         b.in = p->W3, b.out = p->W1, b.odd = 0;
         b.in_pos = P, b.in_batch = 2LL * N * P, b.out_pos = P, b.out_batch = (long long)N * P;
         if ((e = fast::p4<T>(N, b, N, s)) != cudaSuccess) return e;

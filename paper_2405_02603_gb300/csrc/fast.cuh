@@ -275,11 +275,12 @@ __host__ __device__ constexpr int row_pitch(int N) { return ((N + 1) + 15) / 16 
 
 template <int n, int MODE> struct ColGeo {
     static constexpr int N = n / 2, P = row_pitch(N);
+    static constexpr bool ZL = MODE == COL_FMI || MODE == COL_FMO;  // P3: z lines, batch k_y
     static constexpr long long NP = (long long)N * P;
-    static constexpr long long IN_POS = MODE == COL_FMI ? 2 * NP : P;
-    static constexpr long long IN_BATCH = MODE == COL_FWD ? NP : MODE == COL_FMI ? P : 2 * NP;
-    static constexpr long long OUT_POS = MODE == COL_FMI ? 2 * NP : P;
-    static constexpr long long OUT_BATCH = MODE == COL_FWD ? 2 * NP : MODE == COL_FMI ? P : NP;
+    static constexpr long long IN_POS = ZL ? 2 * NP : P;
+    static constexpr long long IN_BATCH = MODE == COL_FWD ? NP : ZL ? P : 2 * NP;
+    static constexpr long long OUT_POS = ZL ? 2 * NP : P;
+    static constexpr long long OUT_BATCH = MODE == COL_FWD ? 2 * NP : ZL ? P : NP;
     static constexpr long long S_POS = (long long)(N + 1) * P, S_BATCH = P;
 };
 
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     // The Nyquist column k_x = N runs in the first X = NB/N block rows, whose
     // tile's L lines are L consecutive batch indices of that one column (their
     // loads are strided, so they go first rather than form the last wave).
-    constexpr int NB = MODE == COL_FMI ? 2 * N : N;  // batch rows (k_y or z)
+    constexpr int NB = G::ZL ? 2 * N : N;  // batch rows (k_y or z)
     constexpr int X = NB / N;
     int line;
     long long bt;
@@ -328,16 +329,17 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     Stg<T, D0, n, V, L>::template compute<R1, 1, HZ0, false>(v, t, tw);
     run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV>(v, buf, t, l, tw, false);
 
-    if constexpr (MODE == COL_FMI) {
+    if constexpr (G::ZL) {
         // multiply by the real, even spectrum at the folded frequency
         // min(p, n - p); for most registers the branch is known at compile time
         const int fy = (int)bt <= N ? (int)bt : n - (int)bt;
         const T *Sy = reinterpret_cast<const T *>(a.S) + (long long)fy * G::S_BATCH + line;
         const T *S_up = Sy + (long long)t * G::S_POS, *S_dn = Sy - (long long)t * G::S_POS;
-        // a field component's odd spectrum: multiplier -i S, negated past the
-        // fold in z (per register, mostly known at compile time) or in k_y
-        const int odd = a.odd;
-        const T sy = odd == 2 && (int)bt > N ? T(-1) : T(1);
+        // COL_FMO (a field component): the spectrum is odd in z (a.odd = 1),
+        // k_y (2) or k_x (3); the multiplier is -i S[fold], negated past the
+        // fold in z (per register) or k_y (per thread); k_x <= N never flips
+        const T sy = MODE == COL_FMO && a.odd == 2 && (int)bt > N ? T(-1) : T(1);
+        const bool oz = MODE == COL_FMO && a.odd == 1;
         StaticFor<0, V / RL>::run([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             StaticFor<0, RL>::run([&](auto rc) {
@@ -357,11 +359,11 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
                     s = ok ? Sy[(long long)fz * G::S_POS] : T(0);
                     upper = p > N;
                 }
-                if (odd == 0) {
+                if constexpr (MODE == COL_FMI) {
                     v[k * RL + r].x *= s;
                     v[k * RL + r].y *= s;
                 } else {
-                    if (odd == 1 && upper) s = -s;
+                    if (oz && upper) s = -s;
                     s *= sy;
                     const C w = v[k * RL + r];
                     v[k * RL + r] = C{s * w.y, -(s * w.x)};
@@ -658,6 +660,12 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
     }                                                                                                          \
     template <> cudaError_t p4<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
         return launch_col<T, COL_INV>(2 * N, a, nb, s);                                                        \
+    }
+
+// the field's P3 (odd spectrum), in translation units of its own
+#define FSP_FAST_FIELD_INSTANTIATE(T)                                                                          \
+    template <> cudaError_t p3_odd<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                        \
+        return launch_col<T, COL_FMO>(2 * N, a, nb, s);                                                        \
     }
 
 }  // namespace fast

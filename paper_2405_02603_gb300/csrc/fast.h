@@ -16,9 +16,9 @@ struct ColArgs {
     const void *S;   // P3: real spectrum S[fold(p)*s_pos + fold(b)*s_batch + c]
     long long s_pos, s_batch;
     int half;        // N
-    // P3: 0 for the potential's even spectrum; 1, 2, 3 for a field
-    // component's spectrum, odd in z (the position), k_y (the batch) or k_x
-    // (the line): the multiplier is -i S[fold], negated where z or k_y > N
+    // p3_odd: 1, 2, 3 for a field component's spectrum odd in z (the
+    // position), k_y (the batch) or k_x (the line): the multiplier is
+    // -i S[fold], negated where z or k_y > N.  Ignored by p3.
     int odd;
 };
 
@@ -33,7 +33,7 @@ struct RowArgs {
     const void *tw2;  // roots of length 2N
 };
 
-enum ColMode { COL_FWD = 0, COL_INV = 1, COL_FMI = 2 };
+enum ColMode { COL_FWD = 0, COL_INV = 1, COL_FMI = 2, COL_FMO = 3 };
 
 // true when the specialised kernels cover this N (N = 32, 64, 128, 256, 512)
 template <typename T> bool has(int N);
@@ -43,6 +43,8 @@ template <typename T> cudaError_t p2(int N, const ColArgs &a, int nbatch, cudaSt
 template <typename T> cudaError_t p3(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 template <typename T> cudaError_t p4(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 template <typename T> cudaError_t p5(int N, const RowArgs &a, cudaStream_t s);
+// P3 of a field component: z-FFT * (-i S_a, odd in the axis a.odd) * z-IFFT
+template <typename T> cudaError_t p3_odd(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 
 }  // namespace fast
 }  // namespace fsp

@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-systems", action="store_true", help="skip the batched and serving legs")
     ap.add_argument("--profile-case", default=None, metavar="DTYPES",
                     help="small profiling case instead of the bench: for each dtype in the comma-separated list "
-                         "(f32, f64, f64df) build an N-grid VG-DCT plan and run two solves of the seeded mixture")
+                         "(f32, f64, f64df; with a '-field' suffix, field solves) build an N-grid VG-DCT plan "
+                         "and run two solves of the seeded mixture")
     return ap.parse_args()
 
 
@@ -71,11 +72,14 @@ def profile_case(args):
     import torch
     import paper_2405_02603_gb300 as fsp
     N = args.n
-    for dtype in args.profile_case.split(","):
+    for case in args.profile_case.split(","):
+        dtype, field = case.split("-")[0], case.endswith("-field")
         plan = fsp.Plan(N, 1.0, "vg_dct", dtype)
+        if field:
+            plan.field_init()
         rho = torch.from_numpy(I.gaussian_mixture(N).astype(np.float32)).to(fsp.torch_dtype(dtype)).cuda()
         for _ in range(2):
-            plan.solve(rho)
+            plan.solve_field(rho) if field else plan.solve(rho)
         torch.cuda.synchronize()
         plan.close()
     print(json.dumps({"profile_case": args.profile_case, "N": N, "ok": True}))

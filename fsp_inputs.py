@@ -68,3 +68,33 @@ def impulse(N, L=1.0, at=(0, 0, 0)):
     rho = np.zeros((N, N, N), dtype=np.float64)
     rho[at[2], at[1], at[0]] = 1.0 / h ** 3
     return rho
+
+
+# ---- non-cubic boxes: n = (n_x, n_y, n_z) cells, box sides L = (L_x, L_y, L_z),
+# arrays of shape (n_z, n_y, n_x) on the cell centres of [-L/2, L/2] per axis
+
+def _r2_3(n, L, centre):
+    z = cell_centres(n[2], L[2])[:, None, None] - centre[2]
+    y = cell_centres(n[1], L[1])[None, :, None] - centre[1]
+    x = cell_centres(n[0], L[0])[None, None, :] - centre[0]
+    return x * x + y * y + z * z
+
+
+def gaussian3(n, L, sigma=0.05, centre=(0.0, 0.0, 0.0), weight=1.0):
+    """The unit-charge Gaussian of `gaussian` on a non-cubic box."""
+    norm = (2.0 * np.pi * sigma * sigma) ** -1.5
+    return weight * norm * np.exp(-_r2_3(n, L, centre) / (2.0 * sigma * sigma))
+
+
+def gaussian_mixture3(n, L, seed=2405, k=8):
+    """The seeded mixture of `gaussian_mixture` on a non-cubic box."""
+    centres, sigmas, weights = mixture_params(seed, k)
+    rho = np.zeros((n[2], n[1], n[0]), dtype=np.float64)
+    for c, s, w in zip(centres, sigmas, weights):
+        rho += gaussian3(n, L, s, tuple(c), w)
+    return rho
+
+
+def random_field3(n, seed=0):
+    """i.i.d. uniform values in [-1, 1], shape (n_z, n_y, n_x)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n[2], n[1], n[0]))

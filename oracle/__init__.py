@@ -22,6 +22,9 @@ error metrics.  Every function names the passage of the paper it follows:
   the Gaussian's field.
 - ``dst1``/``trig1_3d``: type-I DST by definition, and the separable 3D
   DST-I/DCT-I mix an odd kernel's octant needs.
+- ``kernel_T3``, ``solve_fft3``, ``spectrum3``, ``solve_direct3``, ``solve3``:
+  the methods on a non-cubic box of n_x x n_y x n_z cells with spacings
+  h_x, h_y, h_z (the shapes of the paper's weak-scaling runs, Sec. 3.2).
 - ``field_kernel``, ``solve_field_fft``, ``solve_field_direct``,
   ``field_spectrum``, ``solve_field``: the field E = -grad phi (Appendix B,
   Eq. efield) as the convolution of rho with F = -grad G of each method.
@@ -67,6 +70,11 @@ def _load():
         lib.orc_solve_field_fft.argtypes = [i, d, i, dp, dp, dp]
         lib.orc_field_spectrum.argtypes = [i, d, i, dp, dp]
         lib.orc_solve_field_direct.argtypes = [i, d, i, dp, dp, lp, ctypes.c_longlong, dp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.orc_kernel_T3.argtypes = [i, ip, dp, d, dp]
+        lib.orc_solve_fft3.argtypes = [ip, dp, dp, dp, dp]
+        lib.orc_spectrum3.argtypes = [ip, dp, dp, dp]
+        lib.orc_solve_direct3.argtypes = [ip, dp, dp, dp, lp, ctypes.c_longlong, dp]
         _lib = lib
     return _lib
 
@@ -279,10 +287,74 @@ def solve_field(algo, rho, L=1.0, alpha=ALPHA):
     return tuple(solve_field_fft(field_kernel(algo, a, N, L, alpha), a, rho, L / N) for a in range(3))
 
 
+def _dims(n, h):
+    n = (ctypes.c_int * 3)(*[int(v) for v in n])
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    assert h.shape == (3,)
+    return n, h
+
+
+def kernel_T3(algo, n, h, alpha=ALPHA):
+    """Kernel T[m] on a box of n = (n_x, n_y, n_z) cells with spacings
+    h = (h_x, h_y, h_z); shape (n_z+1, n_y+1, n_x+1) indexed [z,y,x]."""
+    algo = ALGOS.get(algo, algo)
+    nn, hh = _dims(n, h)
+    T = np.empty((n[2] + 1, n[1] + 1, n[0] + 1), dtype=np.float64)
+    _load().orc_kernel_T3(int(algo), nn, _p(hh), float(alpha), _p(T))
+    return T
+
+
+def solve_fft3(T, rho, h):
+    """Sec. 2.2 steps 1-5 on the full doubled grid of a non-cubic box."""
+    T, rho = _f64(T), _f64(rho)
+    n = (rho.shape[2], rho.shape[1], rho.shape[0])
+    assert T.shape == (n[2] + 1, n[1] + 1, n[0] + 1)
+    nn, hh = _dims(n, h)
+    phi = np.empty_like(rho)
+    _load().orc_solve_fft3(nn, _p(hh), _p(T), _p(rho), _p(phi))
+    return phi
+
+
+def spectrum3(T, h):
+    """S[q] = h_x h_y h_z DFT{G_2}[q] / (8 n_x n_y n_z) on the octant."""
+    T = _f64(T)
+    n = (T.shape[2] - 1, T.shape[1] - 1, T.shape[0] - 1)
+    nn, hh = _dims(n, h)
+    S = np.empty_like(T)
+    _load().orc_spectrum3(nn, _p(hh), _p(T), _p(S))
+    return S
+
+
+def solve_direct3(T, rho, h, points=None):
+    """phi_i = h_x h_y h_z sum_j T[|i-j|] rho_j at flat indices (or all)."""
+    T, rho = _f64(T), _f64(rho)
+    n = (rho.shape[2], rho.shape[1], rho.shape[0])
+    assert T.shape == (n[2] + 1, n[1] + 1, n[0] + 1)
+    nn, hh = _dims(n, h)
+    lib = _load()
+    if points is None:
+        out = np.empty_like(rho)
+        lib.orc_solve_direct3(nn, _p(hh), _p(T), _p(rho), None, 0, _p(out))
+        return out
+    pts = np.ascontiguousarray(points, dtype=np.int64).ravel()
+    assert pts.size == 0 or (pts.min() >= 0 and pts.max() < rho.size)
+    out = np.empty(pts.size, dtype=np.float64)
+    lib.orc_solve_direct3(nn, _p(hh), _p(T), _p(rho), pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                          pts.size, _p(out))
+    return out
+
+
+def solve3(algo, rho, h, alpha=ALPHA):
+    """Kernel plus FFT solve on a non-cubic box (rho indexed [z,y,x])."""
+    n = (rho.shape[2], rho.shape[1], rho.shape[0])
+    return solve_fft3(kernel_T3(algo, n, h, alpha), rho, h)
+
+
 from . import analytic  # noqa: E402  (pure-numpy helpers, no C)
 
 __all__ = ["HE", "VG", "VG_DCT", "ALPHA", "dft1d", "fft1d", "fft3d", "dct1", "dct1_3d",
            "green_vico_hat", "window", "kernel_T", "vg_full", "spectrum", "solve_fft",
            "solve_direct", "solve", "analytic", "num_threads", "set_num_threads", "dst1", "trig1_3d",
-           "field_kernel", "solve_field_fft", "field_spectrum", "solve_field_direct", "solve_field"]
+           "field_kernel", "solve_field_fft", "field_spectrum", "solve_field_direct", "solve_field",
+           "kernel_T3", "solve_fft3", "spectrum3", "solve_direct3", "solve3"]
 

@@ -81,3 +81,18 @@ def gaussian_field(N, L=1.0, sigma=0.05, centre=(0.0, 0.0, 0.0), weight=1.0):
     q = erf(s / np.sqrt(2.0)) - np.sqrt(2.0 / np.pi) * s * np.exp(-0.5 * s * s)
     er_over_r = np.where(r > 1e-12, q / (4.0 * np.pi * np.maximum(r, 1e-300) ** 3), 0.0)
     return tuple(weight * er_over_r * d for d in (x, y, z))
+
+
+def gaussian_potential3(n, L, sigma=0.05, centre=(0.0, 0.0, 0.0), weight=1.0):
+    """gaussian_potential on a non-cubic box of n = (n_x, n_y, n_z) cells and
+    sides L = (L_x, L_y, L_z); shape (n_z, n_y, n_x)."""
+    z = cell_centres(n[2], L[2])[:, None, None] - centre[2]
+    y = cell_centres(n[1], L[1])[None, :, None] - centre[1]
+    x = cell_centres(n[0], L[0])[None, None, :] - centre[0]
+    r = np.sqrt(x * x + y * y + z * z)
+    out = np.empty_like(r)
+    small = r < 1e-12
+    rr = r[~small]
+    out[~small] = erf(rr / (np.sqrt(2.0) * sigma)) / (4.0 * np.pi * rr)
+    out[small] = np.sqrt(2.0 / np.pi) / (4.0 * np.pi * sigma)
+    return weight * out

@@ -28,6 +28,11 @@
  *                        G_2, multiply, inverse FFT, scale by h^3, restrict.
  *   - orc_solve_direct : the discrete convolution phi_i = h^3 sum_j T[i-j] rho_j
  *                        evaluated term by term (Sec. 1, the O(N_g^2) sum).
+ *   - orc_kernel_T3, orc_spectrum3, orc_solve_fft3, orc_solve_direct3 : the
+ *                        same method on a box of N_x x N_y x N_z cells with
+ *                        spacings h_x, h_y, h_z (the non-cubic grids the
+ *                        paper's weak-scaling runs use, Sec. 3.2); the window
+ *                        is alpha times the box diagonal.
  *   - orc_dst1_1d, orc_trig1_3d, orc_field_kernel, orc_solve_field_fft,
  *     orc_field_spectrum, orc_solve_field_direct : the field E = -grad phi of
  *                        Appendix B (Eq. efield), as the convolution of rho
@@ -680,5 +685,156 @@ void orc_solve_field_direct(int N, double h, int a, const double *F, const doubl
                 }
             }
         out[p] = h * h * h * (sum + comp);
+    }
+}
+
+/* ------------------------------------------------- non-cubic boxes -- */
+/*
+ * The methods on a box of n[0] x n[1] x n[2] cells (x, y, z) with spacings
+ * h[0], h[1], h[2]: the same definitions per axis, with N and h of that axis.
+ * Arrays are (n_z, n_y, n_x) with x fastest; kernels and spectra are
+ * (n_z+1, n_y+1, n_x+1).
+ *   HE:     T[m] = 1/(4 pi |(m_x h_x, m_y h_y, m_z h_z)|), T[0] = 1/(4 pi).
+ *   VG:     G_L sampled on the (4n_x, 4n_y, 4n_z) frequency grid,
+ *           k_a = 2 pi j_a / (4 n_a h_a), j_a in [-2n_a, 2n_a), inverse DFT,
+ *           scaled by 1 / prod_a (4 n_a h_a), restricted to [0,n_a] per axis.
+ *           The window is L_t = alpha |(L_x, L_y, L_z)| (alpha sqrt(3) L for a
+ *           cube), L_a = n_a h_a.
+ *   VG-DCT: the same through the (2n_a+1) octant and a DCT-I per axis.
+ */
+void orc_kernel_T3(int algo, const int *n, const double *h, double alpha, double *T) {
+    int k[3] = {n[0] + 1, n[1] + 1, n[2] + 1};
+    double Lb[3] = {n[0] * h[0], n[1] * h[1], n[2] * h[2]};
+    double Lt = alpha * sqrt(Lb[0] * Lb[0] + Lb[1] * Lb[1] + Lb[2] * Lb[2]);
+    if (algo == ORC_HE) {
+        for (int z = 0; z < k[2]; ++z)
+            for (int y = 0; y < k[1]; ++y)
+                for (int x = 0; x < k[0]; ++x) {
+                    double dx = x * h[0], dy = y * h[1], dz = z * h[2];
+                    T[((size_t)z * k[1] + y) * k[0] + x] =
+                        (x | y | z) ? green_free(sqrt(dx * dx + dy * dy + dz * dz)) : 1.0 / (4.0 * ORC_PI);
+                }
+    } else if (algo == ORC_VG) {
+        int m[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
+        size_t tot = (size_t)m[0] * m[1] * m[2];
+        cplx *g = (cplx *)malloc(sizeof(cplx) * tot);
+        double dk[3];
+        for (int a = 0; a < 3; ++a) dk[a] = 2.0 * ORC_PI / ((double)m[a] * h[a]);
+#pragma omp parallel for schedule(static)
+        for (long long idx = 0; idx < (long long)tot; ++idx) {
+            int s3[3] = {(int)(idx % m[0]), (int)((idx / m[0]) % m[1]), (int)(idx / ((long long)m[0] * m[1]))};
+            double k2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                int j = s3[a] < 2 * n[a] ? s3[a] : s3[a] - m[a];
+                k2 += (dk[a] * j) * (dk[a] * j);
+            }
+            g[idx] = orc_green_vico_hat(sqrt(k2), Lt);
+        }
+        orc_fft3d(m[0], m[1], m[2], g, +1);
+        double scale = 1.0 / (((double)m[0] * h[0]) * ((double)m[1] * h[1]) * ((double)m[2] * h[2]));
+        for (int z = 0; z < k[2]; ++z)
+            for (int y = 0; y < k[1]; ++y)
+                for (int x = 0; x < k[0]; ++x)
+                    T[((size_t)z * k[1] + y) * k[0] + x] = creal(g[((size_t)z * m[1] + y) * m[0] + x]) * scale;
+        free(g);
+    } else {
+        int M[3] = {2 * n[0], 2 * n[1], 2 * n[2]}, q[3] = {M[0] + 1, M[1] + 1, M[2] + 1};
+        double dk[3];
+        for (int a = 0; a < 3; ++a) dk[a] = 2.0 * ORC_PI / (4.0 * n[a] * h[a]);
+        double *g = (double *)malloc(sizeof(double) * (size_t)q[0] * q[1] * q[2]);
+        for (int z = 0; z < q[2]; ++z)
+            for (int y = 0; y < q[1]; ++y)
+                for (int x = 0; x < q[0]; ++x) {
+                    double kx = dk[0] * x, ky = dk[1] * y, kz = dk[2] * z;
+                    g[((size_t)z * q[1] + y) * q[0] + x] = orc_green_vico_hat(sqrt(kx * kx + ky * ky + kz * kz), Lt);
+                }
+        /* DCT-I along x, y, z in turn, each keeping outputs [0, n_a] */
+        double *t1 = (double *)malloc(sizeof(double) * (size_t)k[0] * q[1] * q[2]);
+        double *t2 = (double *)malloc(sizeof(double) * (size_t)k[0] * k[1] * q[2]);
+        axis_trig(M[0], n[0], 0, 0, q[0], q[1], q[2], g, t1);
+        axis_trig(M[1], n[1], 0, 1, k[0], q[1], q[2], t1, t2);
+        axis_trig(M[2], n[2], 0, 2, k[0], k[1], q[2], t2, T);
+        double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[1] * h[1]) * (4.0 * n[2] * h[2]));
+        for (size_t i = 0; i < (size_t)k[0] * k[1] * k[2]; ++i) T[i] *= scale;
+        free(t2);
+        free(t1);
+        free(g);
+    }
+}
+
+/* G_2 on the (2n_x, 2n_y, 2n_z) doubled grid from the octant T. */
+static void doubled3(const int *n, const double *T, cplx *g2) {
+    int d[3] = {2 * n[0], 2 * n[1], 2 * n[2]}, k[3] = {n[0] + 1, n[1] + 1, n[2] + 1};
+    for (int z = 0; z < d[2]; ++z)
+        for (int y = 0; y < d[1]; ++y)
+            for (int x = 0; x < d[0]; ++x)
+                g2[((size_t)z * d[1] + y) * d[0] + x] =
+                    T[((size_t)fold2(z, n[2]) * k[1] + fold2(y, n[1])) * k[0] + fold2(x, n[0])];
+}
+
+/* Sec. 2.2 steps 1-5 on the full (2n_x, 2n_y, 2n_z) complex grid. */
+void orc_solve_fft3(const int *n, const double *h, const double *T, const double *rho, double *phi) {
+    int d[3] = {2 * n[0], 2 * n[1], 2 * n[2]};
+    size_t tot = (size_t)d[0] * d[1] * d[2];
+    cplx *r2 = (cplx *)calloc(tot, sizeof(cplx));
+    cplx *g2 = (cplx *)malloc(sizeof(cplx) * tot);
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x)
+                r2[((size_t)z * d[1] + y) * d[0] + x] = rho[((size_t)z * n[1] + y) * n[0] + x];
+    doubled3(n, T, g2);
+    orc_fft3d(d[0], d[1], d[2], r2, -1);
+    orc_fft3d(d[0], d[1], d[2], g2, -1);
+    for (size_t i = 0; i < tot; ++i) r2[i] *= g2[i];
+    orc_fft3d(d[0], d[1], d[2], r2, +1);
+    double scale = h[0] * h[1] * h[2] / (double)tot;
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x)
+                phi[((size_t)z * n[1] + y) * n[0] + x] = creal(r2[((size_t)z * d[1] + y) * d[0] + x]) * scale;
+    free(g2);
+    free(r2);
+}
+
+/* S[q] = h_x h_y h_z / (8 n_x n_y n_z) * DFT{G_2}[q], q in the octant (real part). */
+void orc_spectrum3(const int *n, const double *h, const double *T, double *S) {
+    int d[3] = {2 * n[0], 2 * n[1], 2 * n[2]}, k[3] = {n[0] + 1, n[1] + 1, n[2] + 1};
+    size_t tot = (size_t)d[0] * d[1] * d[2];
+    cplx *g2 = (cplx *)malloc(sizeof(cplx) * tot);
+    doubled3(n, T, g2);
+    orc_fft3d(d[0], d[1], d[2], g2, -1);
+    double scale = h[0] * h[1] * h[2] / (double)tot;
+    for (int z = 0; z < k[2]; ++z)
+        for (int y = 0; y < k[1]; ++y)
+            for (int x = 0; x < k[0]; ++x)
+                S[((size_t)z * k[1] + y) * k[0] + x] = creal(g2[((size_t)z * d[1] + y) * d[0] + x]) * scale;
+    free(g2);
+}
+
+/* phi_i = h_x h_y h_z sum_j T[|i - j|] rho_j by its definition (Neumaier). */
+void orc_solve_direct3(const int *n, const double *h, const double *T, const double *rho, const long long *pts,
+                       long long npts, double *out) {
+    int k[3] = {n[0] + 1, n[1] + 1, n[2] + 1};
+    long long total = pts ? npts : (long long)n[0] * n[1] * n[2];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long p = 0; p < total; ++p) {
+        long long i = pts ? pts[p] : p;
+        int ix = (int)(i % n[0]), iy = (int)((i / n[0]) % n[1]), iz = (int)(i / ((long long)n[0] * n[1]));
+        double sum = 0.0, comp = 0.0;
+        for (int jz = 0; jz < n[2]; ++jz)
+            for (int jy = 0; jy < n[1]; ++jy) {
+                const double *Trow = T + ((size_t)abs(iz - jz) * k[1] + abs(iy - jy)) * k[0];
+                const double *rrow = rho + ((size_t)jz * n[1] + jy) * n[0];
+                for (int jx = 0; jx < n[0]; ++jx) {
+                    double t = Trow[abs(ix - jx)] * rrow[jx];
+                    double s = sum + t;
+                    if (fabs(sum) >= fabs(t))
+                        comp += (sum - s) + t;
+                    else
+                        comp += (t - s) + sum;
+                    sum = s;
+                }
+            }
+        out[p] = h[0] * h[1] * h[2] * (sum + comp);
     }
 }

@@ -7,7 +7,9 @@ coefficient, a wrong stride, a padding bound), builds it with gcc on the CPU
 and runs the pins against it: at least one must fail.  The mistakes are made
 in a temporary copy; the oracle itself is never modified.  The field
 functions have their own planted mistakes (a lost odd extension, a wrong
-power or sign or axis of the field kernel, a wrong DST factor) and pins.
+power or sign or axis of the field kernel, a wrong DST factor) and pins, and
+so do the non-cubic ones (one axis's size or spacing used for another, the
+cubic window, a wrong fold, scale or transform order).
 """
 import ctypes
 import os
@@ -174,6 +176,70 @@ def _field_pins(orc):
     return res
 
 
+# planted mistakes in the non-cubic functions (caught by _aniso_pins)
+ANISO_MUTANTS = [
+    ("he3_spacing_axis", "double dx = x * h[0], dy = y * h[1], dz = z * h[2];",
+     "double dx = x * h[0], dy = y * h[0], dz = z * h[2];"),
+    ("vg3_dk_axis", "for (int a = 0; a < 3; ++a) dk[a] = 2.0 * ORC_PI / ((double)m[a] * h[a]);",
+     "for (int a = 0; a < 3; ++a) dk[a] = 2.0 * ORC_PI / ((double)m[a] * h[0]);"),
+    ("vgdct3_dk_size", "for (int a = 0; a < 3; ++a) dk[a] = 2.0 * ORC_PI / (4.0 * n[a] * h[a]);",
+     "for (int a = 0; a < 3; ++a) dk[a] = 2.0 * ORC_PI / (4.0 * n[0] * h[a]);"),
+    ("window_cubic", "double Lt = alpha * sqrt(Lb[0] * Lb[0] + Lb[1] * Lb[1] + Lb[2] * Lb[2]);",
+     "double Lt = alpha * sqrt(3.0) * Lb[0];"),
+    ("doubled3_fold_axis", "T[((size_t)fold2(z, n[2]) * k[1] + fold2(y, n[1])) * k[0] + fold2(x, n[0])];",
+     "T[((size_t)fold2(z, n[2]) * k[1] + fold2(y, n[0])) * k[0] + fold2(x, n[0])];"),
+    ("solve3_scale", "double scale = h[0] * h[1] * h[2] / (double)tot;\n    for (int z = 0; z < n[2]; ++z)",
+     "double scale = h[0] * h[0] * h[0] / (double)tot;\n    for (int z = 0; z < n[2]; ++z)"),
+    ("vgdct3_scale_axis", "double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[1] * h[1]) * (4.0 * n[2] * h[2]));",
+     "double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[0] * h[1]) * (4.0 * n[2] * h[2]));"),
+]
+
+
+def _aniso_pins(orc):
+    """Name -> passed, for a cheap set of the non-cubic pins."""
+    from oracle import analytic as A
+    res = {}
+    n, h = (6, 4, 5), (0.2, 0.3, 0.25)
+    T = orc.kernel_T("vg_dct", 5)
+    res["cube_equals_cubic"] = np.allclose(orc.kernel_T3("vg_dct", (5, 5, 5), (0.2,) * 3), T, rtol=1e-12, atol=1e-15)
+    ok = True
+    for algo in ("he", "vg_dct"):
+        T3 = orc.kernel_T3(algo, n, h)
+        rho = I.random_field3(n, 2)
+        b = orc.solve_direct3(T3, rho, h)
+        ok = ok and np.allclose(orc.solve_fft3(T3, rho, h), b, rtol=0, atol=1e-12 * np.abs(b).max())
+    res["fft_eq_direct"] = ok
+    res["vg_two_routes"] = np.allclose(orc.kernel_T3("vg", n, h), orc.kernel_T3("vg_dct", n, h), rtol=0,
+                                       atol=1e-12 * np.abs(orc.kernel_T3("vg", n, h)).max())
+    ok = True
+    for algo in ("he", "vg_dct"):
+        T3 = orc.kernel_T3(algo, n, h)
+        ok = ok and np.allclose(orc.kernel_T3(algo, (n[1], n[0], n[2]), (h[1], h[0], h[2])), np.swapaxes(T3, 1, 2),
+                                rtol=1e-10, atol=1e-14)
+    res["axis_exchange"] = ok
+    nn, hh, j = (7, 5, 6), (0.1, 0.17, 0.13), (2, 4, 1)
+    rho = np.zeros((nn[2], nn[1], nn[0]))
+    rho[j[2], j[1], j[0]] = 1.0 / (hh[0] * hh[1] * hh[2])
+    z, y, x = np.meshgrid(np.arange(nn[2]), np.arange(nn[1]), np.arange(nn[0]), indexing="ij")
+    r = np.sqrt(((x - j[0]) * hh[0]) ** 2 + ((y - j[1]) * hh[1]) ** 2 + ((z - j[2]) * hh[2]) ** 2)
+    want = np.where(r > 0, 1.0 / (4 * np.pi * np.where(r > 0, r, 1.0)), 1.0 / (4 * np.pi))
+    res["he_impulse"] = np.allclose(orc.solve3("he", rho, hh), want, rtol=1e-10)
+    ng, Lg = (24, 16, 32), (1.0, 0.8, 1.2)
+    hg = tuple(Lg[a] / ng[a] for a in range(3))
+    e = A.e_max(orc.solve3("vg_dct", I.gaussian3(ng, Lg, 0.08), hg), A.gaussian_potential3(ng, Lg, 0.08))
+    res["gaussian_vg"] = e < 1e-6
+    nf, Lf, c = (16, 16, 32), (1.0, 1.0, 2.0), (-0.25, -0.25, -0.75)
+    hf = tuple(Lf[a] / nf[a] for a in range(3))
+    phi = orc.solve3("vg_dct", I.gaussian3(nf, Lf, 0.05, c), hf)
+    ex = A.gaussian_potential3(nf, Lf, 0.05, c)
+    zz = I.cell_centres(nf[2], Lf[2])[:, None, None] - c[2]
+    yy = I.cell_centres(nf[1], Lf[1])[None, :, None] - c[1]
+    xx = I.cell_centres(nf[0], Lf[0])[None, None, :] - c[0]
+    far = np.sqrt(xx * xx + yy * yy + zz * zz) > 1.2
+    res["far_field"] = float(np.max(np.abs(phi[far] - ex[far]) / ex[far])) < 1e-2
+    return res
+
+
 @pytest.fixture(scope="module")
 def baseline(orc):
     return _pins(orc)
@@ -204,6 +270,18 @@ def _run_mutant(orc, name, old, new, pins):
             orc._lib = saved
         del mutant
     return res
+
+
+def test_aniso_pins_pass_on_the_oracle(orc):
+    res = _aniso_pins(orc)
+    assert all(res.values()), res
+
+
+@pytest.mark.parametrize("name,old,new", ANISO_MUTANTS, ids=[m[0] for m in ANISO_MUTANTS])
+def test_planted_aniso_mistake_fails_a_pin(orc, name, old, new):
+    res = _run_mutant(orc, name, old, new, _aniso_pins)
+    failed = [k for k, ok in res.items() if not ok]
+    assert failed, "no non-cubic pin caught the planted mistake " + name
 
 
 @pytest.mark.parametrize("name,old,new", FIELD_MUTANTS, ids=[m[0] for m in FIELD_MUTANTS])

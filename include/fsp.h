@@ -96,6 +96,32 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
                            fsp_stream stream);
 
 /*
+ * fsp_plan_create_aniso -- a plan for a non-cubic box of nx x ny x nz cells
+ * with spacings hx, hy, hz (sides L_a = n_a h_a), such as the 512^2 x 1024
+ * grids of the paper's weak-scaling runs (Sec. 3.2).  The methods of
+ * Sec. 2.2-2.4 per axis: HE samples 1/(4 pi |(m_x hx, m_y hy, m_z hz)|) with
+ * T[0] = 1/(4 pi); VG and VG-DCT sample G_L on the (4 n_a) frequency grid
+ * k_a = 2 pi j_a / (4 n_a h_a) (resp. its octant) with the window
+ * L_t = 1.1 |(L_x, L_y, L_z)| (1.1 sqrt(3) L for a cube).  Layout of rho and
+ * phi: nz x ny x nx reals, x fastest.
+ *
+ * A cube (nx = ny = nz, hx = hy = hz) returns the cubic plan of
+ * fsp_plan_create, with its specialised kernels.  Otherwise the solve runs on
+ * the generic engine (any 2/3/5-smooth 2 n_a, and 4 n_a for FSP_VG); dtype
+ * FSP_F64 or FSP_F32_MIXED (FSP_F64_DF: FSP_EUNSUPPORTED).  FSP_VG and
+ * FSP_VG_DCT need 3 min_a L_a >= L_t (the (4 n_a h_a)-periodic images of the
+ * truncated kernel must stay outside the box): FSP_EUNSUPPORTED otherwise,
+ * e.g. for a 1 x 1 x a box with a > 2.33.  The workspace is
+ * 3 nz ny P complex values (P = nx+1 rounded up to 16), the spectrum
+ * (nz+1)(ny+1)P reals.  fsp_solve, fsp_solve_host(_many), fsp_plan_sync,
+ * fsp_plan_set_timing, fsp_plan_spectrum ((nz+1)(ny+1)(nx+1) doubles) and
+ * fsp_plan_destroy accept the plan; field solves and batches
+ * (fsp_plan_field_init, fsp_batch_create) return FSP_EUNSUPPORTED for it.
+ */
+fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double hx, double hy, double hz,
+                                 fsp_algo algo, fsp_dtype dtype, fsp_stream stream);
+
+/*
  * fsp_solve -- one free-space solve, phi = G * rho (Sec. 2.2 steps 1-5):
  * zero-pad to (2N)^3 (never materialised), 3D real-to-complex FFT, multiply
  * by the plan's spectrum, inverse FFT, restrict to N^3.  Five kernel launches

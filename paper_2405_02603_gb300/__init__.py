@@ -59,6 +59,7 @@ def lib(build_if_missing=True):
     L.fsp_status_str.restype = ctypes.c_char_p
     L.fsp_status_str.argtypes = [i]
     L.fsp_plan_create.argtypes = [ctypes.POINTER(vp), i, d, d, i, i, vp]
+    L.fsp_plan_create_aniso.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, d, i, i, vp]
     L.fsp_solve.argtypes = [vp, vp, vp, vp]
     L.fsp_solve_host.argtypes = [vp, vp, vp, vp]
     L.fsp_solve_host_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
@@ -105,7 +106,7 @@ def lib(build_if_missing=True):
     for name in ("fsp_batch_create", "fsp_batch_launch", "fsp_batch_wait", "fsp_batch_set_timeout",
                  "fsp_batch_inject_stall", "fsp_batch_destroy", "fsp_solve_batched"):
         getattr(L, name).restype = i
-    for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
+    for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_plan_create_aniso", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
                  "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc", "fsp_plan_field_init",
                  "fsp_solve_field"):
         getattr(L, name).restype = i
@@ -142,15 +143,32 @@ def torch_dtype(dtype):
 
 
 class Plan:
-    """One solver instance for (N, L, algo, dtype): fsp_plan_create / fsp_solve / fsp_plan_destroy."""
+    """One solver instance for (N, L, algo, dtype): fsp_plan_create / fsp_solve / fsp_plan_destroy.
+
+    N and L may also be 3-sequences (n_x, n_y, n_z) and (L_x, L_y, L_z): a
+    non-cubic box (fsp_plan_create_aniso), arrays of shape (n_z, n_y, n_x)."""
 
     def __init__(self, N, L=1.0, algo="vg_dct", dtype="f64", h=None, stream=None):
-        self.N, self.L = int(N), float(L)
         self.algo, self.dtype = algo, dtype
-        self.h = self.L / self.N if h is None else float(h)
         self._p = ctypes.c_void_p()
-        check(lib().fsp_plan_create(ctypes.byref(self._p), self.N, self.L, self.h, _algo_code(algo),
-                                    _dtype_code(dtype), _stream_handle(stream)), "fsp_plan_create")
+        if isinstance(N, (tuple, list)):
+            n = tuple(int(v) for v in N)
+            Ls = tuple(float(v) for v in L) if isinstance(L, (tuple, list)) else (float(L),) * 3
+            hs = tuple(Ls[a] / n[a] for a in range(3)) if h is None else tuple(float(v) for v in h)
+            self.n3, self.h3, self.L3 = n, hs, Ls
+            self.N, self.L, self.h = n[0], Ls[0], hs[0]
+            self.shape = (n[2], n[1], n[0])
+            check(lib().fsp_plan_create_aniso(ctypes.byref(self._p), n[0], n[1], n[2], hs[0], hs[1], hs[2],
+                                              _algo_code(algo), _dtype_code(dtype), _stream_handle(stream)),
+                  "fsp_plan_create_aniso")
+        else:
+            self.N, self.L = int(N), float(L)
+            self.h = self.L / self.N if h is None else float(h)
+            self.n3, self.h3, self.L3 = (self.N,) * 3, (self.h,) * 3, (self.L,) * 3
+            self.shape = (self.N,) * 3
+            check(lib().fsp_plan_create(ctypes.byref(self._p), self.N, self.L, self.h, _algo_code(algo),
+                                        _dtype_code(dtype), _stream_handle(stream)), "fsp_plan_create")
+        self.npoints = self.shape[0] * self.shape[1] * self.shape[2]
 
     @property
     def handle(self):
@@ -220,7 +238,7 @@ class Plan:
 
     def spectrum(self):
         import numpy as np
-        out = np.empty((self.N + 1,) * 3, dtype=np.float64)
+        out = np.empty(tuple(d + 1 for d in self.shape), dtype=np.float64)
         check(lib().fsp_plan_spectrum(self._p, ctypes.c_void_p(out.ctypes.data)), "fsp_plan_spectrum")
         return out
 
@@ -251,9 +269,9 @@ class Plan:
 
     def _check_tensor(self, t):
         import torch
-        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch_dtype(self.dtype) and t.numel() == self.N ** 3):
-            raise FspError(FSP_EINVAL, "tensor must be a contiguous CUDA %s tensor of N^3 elements"
-                           % torch_dtype(self.dtype))
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch_dtype(self.dtype) and t.numel() == self.npoints):
+            raise FspError(FSP_EINVAL, "tensor must be a contiguous CUDA %s tensor of %d elements"
+                           % (torch_dtype(self.dtype), self.npoints))
 
 
 def kernel_T(N, L=1.0, algo="vg_dct", stream=None):

@@ -151,8 +151,31 @@ fsp_status roots_f64(DevBuf &b, int n, cudaStream_t s) {
 // Real-space kernel T[m], m in [0,N]^3, into t_dev (FP64).  Asynchronous on s;
 // temporaries are owned by `keep` and must outlive the enqueued work.
 struct Temps {
-    DevBuf g, a1, a2, tw;
+    DevBuf g, a1, a2, tw, tw_y, tw_z;
 };
+
+// Roots tables of lengths len[0..2] (FP64): one per distinct length, so that
+// a cube uses a single table; tab[a] points at axis a's.
+fsp_status roots_3(Temps &tmp, const int *len, const void **tab, cudaStream_t s) {
+    fsp_status st;
+    if ((st = roots_f64(tmp.tw, len[0], s)) != FSP_OK) return st;
+    tab[0] = tmp.tw.p;
+    if (len[1] == len[0]) {
+        tab[1] = tmp.tw.p;
+    } else {
+        if ((st = roots_f64(tmp.tw_y, len[1], s)) != FSP_OK) return st;
+        tab[1] = tmp.tw_y.p;
+    }
+    if (len[2] == len[0]) {
+        tab[2] = tmp.tw.p;
+    } else if (len[2] == len[1]) {
+        tab[2] = tab[1];
+    } else {
+        if ((st = roots_f64(tmp.tw_z, len[2], s)) != FSP_OK) return st;
+        tab[2] = tmp.tw_z.p;
+    }
+    return FSP_OK;
+}
 
 // DCT-I (kind false) or DST-I (kind true) of real lines, FP64.
 cudaError_t launch_trig(bool dst, const LinesArgs &a, cudaStream_t s) {
@@ -160,46 +183,90 @@ cudaError_t launch_trig(bool dst, const LinesArgs &a, cudaStream_t s) {
                : launch_lines<double, IN_REAL_EVEN, OUT_REAL, M_FWD>(a, s);
 }
 
-// Separable transform of the (2N+1)^3 octant g (M = 2N samples per axis,
-// extended to 4N): DST-I along axis `odd` (0 = x, 1 = y, 2 = z; -1: none) and
-// DCT-I along the others, outputs [0,N] per axis into out ((N+1)^3), FP64.
-// This is the (4N)^3 DFT of a sequence even (or, along `odd`, odd) in every
-// axis (Sec. 2.4).  Temporaries in tmp.a1, tmp.a2, tmp.tw.
-fsp_status enqueue_octant_transform(int N, int odd, const double *g, double *out, cudaStream_t s, Temps &tmp) {
-    const int k1 = N + 1, M = 2 * N, nm = M + 1, n = 2 * M;
+// Separable transform of the octant g of (2n_x+1, 2n_y+1, 2n_z+1) samples
+// (M_a = 2n_a per axis, extended to 4n_a): DST-I along axis `odd` (0 = x,
+// 1 = y, 2 = z; -1: none) and DCT-I along the others, outputs [0,n_a] per
+// axis into out ((n_z+1)(n_y+1)(n_x+1)), FP64.  This is the (4n)^3 DFT of a
+// sequence even (or, along `odd`, odd) in every axis (Sec. 2.4).
+// Temporaries in tmp.a1, tmp.a2 and the roots tables.
+fsp_status enqueue_octant_transform3(const int *nn, int odd, const double *g, double *out, cudaStream_t s, Temps &tmp) {
+    const int k[3] = {nn[0] + 1, nn[1] + 1, nn[2] + 1};
+    const int q[3] = {2 * nn[0] + 1, 2 * nn[1] + 1, 2 * nn[2] + 1};
+    const int len[3] = {4 * nn[0], 4 * nn[1], 4 * nn[2]};
     fsp_status st;
-    TileCfg cr, cc;
-    if (!make_cfg(n, n, sizeof(double2), 3, cr) || !make_cfg(n, n, sizeof(double2), 3, cc)) return FSP_EUNSUPPORTED;
-    if ((st = alloc_or_nomem(tmp.a1, sizeof(double) * (size_t)nm * nm * k1)) != FSP_OK) return st;
-    if ((st = alloc_or_nomem(tmp.a2, sizeof(double) * (size_t)nm * k1 * k1)) != FSP_OK) return st;
-    if ((st = roots_f64(tmp.tw, n, s)) != FSP_OK) return st;
+    TileCfg c[3];
+    for (int a = 0; a < 3; ++a)
+        if (!make_cfg(len[a], len[a], sizeof(double2), 3, c[a])) return FSP_EUNSUPPORTED;
+    if ((st = alloc_or_nomem(tmp.a1, sizeof(double) * (size_t)q[2] * q[1] * k[0])) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(tmp.a2, sizeof(double) * (size_t)q[2] * k[1] * k[0])) != FSP_OK) return st;
+    const void *tab[3];
+    if ((st = roots_3(tmp, len, tab, s)) != FSP_OK) return st;
     LinesArgs a{};
-    a.tw = tmp.tw.p;
-    a.st = cr.st;
-    a.tpl = cr.tpl;
-    a.lgL = cr.lgL;
-    // x: rows of M+1 reals -> rows of N+1
+    // x: rows of q_x reals -> rows of k_x
+    a.tw = tab[0], a.st = c[0].st, a.tpl = c[0].tpl, a.lgL = c[0].lgL;
     a.in = g;
     a.out = tmp.a1.p;
-    a.in_pos = 1, a.in_line = nm, a.in_batch = 0;
-    a.out_pos = 1, a.out_line = k1, a.out_batch = 0;
-    a.n_out = k1, a.nlines = nm * nm, a.nbatch = 1;
+    a.in_pos = 1, a.in_line = q[0], a.in_batch = 0;
+    a.out_pos = 1, a.out_line = k[0], a.out_batch = 0;
+    a.n_out = k[0], a.nlines = q[1] * q[2], a.nbatch = 1;
     FSP_TRY_CUDA(launch_trig(odd == 0, a, s));
-    // y: columns (x in [0,N]) of a1[z][y][x]
-    a.tpl = cc.tpl, a.lgL = cc.lgL;
+    // y: columns (x in [0,n_x]) of a1[z][y][x]
+    a.tw = tab[1], a.st = c[1].st, a.tpl = c[1].tpl, a.lgL = c[1].lgL;
     a.in = tmp.a1.p;
     a.out = tmp.a2.p;
-    a.in_pos = k1, a.in_line = 1, a.in_batch = (long long)nm * k1;
-    a.out_pos = k1, a.out_line = 1, a.out_batch = (long long)k1 * k1;
-    a.n_out = k1, a.nlines = k1, a.nbatch = nm;
+    a.in_pos = k[0], a.in_line = 1, a.in_batch = (long long)q[1] * k[0];
+    a.out_pos = k[0], a.out_line = 1, a.out_batch = (long long)k[1] * k[0];
+    a.n_out = k[1], a.nlines = k[0], a.nbatch = q[2];
     FSP_TRY_CUDA(launch_trig(odd == 1, a, s));
     // z: columns of a2[z][y][x], batch y
+    a.tw = tab[2], a.st = c[2].st, a.tpl = c[2].tpl, a.lgL = c[2].lgL;
     a.in = tmp.a2.p;
     a.out = out;
-    a.in_pos = (long long)k1 * k1, a.in_line = 1, a.in_batch = k1;
-    a.out_pos = (long long)k1 * k1, a.out_line = 1, a.out_batch = k1;
-    a.n_out = k1, a.nlines = k1, a.nbatch = k1;
+    a.in_pos = (long long)k[1] * k[0], a.in_line = 1, a.in_batch = k[0];
+    a.out_pos = (long long)k[1] * k[0], a.out_line = 1, a.out_batch = k[0];
+    a.n_out = k[2], a.nlines = k[0], a.nbatch = k[1];
     FSP_TRY_CUDA(launch_trig(odd == 2, a, s));
+    return FSP_OK;
+}
+
+fsp_status enqueue_octant_transform(int N, int odd, const double *g, double *out, cudaStream_t s, Temps &tmp) {
+    const int nn[3] = {N, N, N};
+    return enqueue_octant_transform3(nn, odd, g, out, s, tmp);
+}
+
+// Vico-Greengard on the (4n_x, 4n_y, 4n_z) grid (Sec. 2.3): the sampled G_L in
+// tmp.g (complex), unnormalised inverse DFT per axis keeping outputs [0,n_a]
+// (three pruned passes), real part into t_dev, unscaled.
+fsp_status enqueue_vg_inverse3(const int *nn, double *t_dev, cudaStream_t s, Temps &tmp) {
+    const int k[3] = {nn[0] + 1, nn[1] + 1, nn[2] + 1};
+    const int m[3] = {4 * nn[0], 4 * nn[1], 4 * nn[2]};
+    fsp_status st;
+    TileCfg c[3];
+    for (int a = 0; a < 3; ++a)
+        if (!make_cfg(m[a], m[a], sizeof(double2), 3, c[a])) return FSP_EUNSUPPORTED;
+    if ((st = alloc_or_nomem(tmp.a1, sizeof(double2) * (size_t)m[2] * m[1] * k[0])) != FSP_OK) return st;
+    if ((st = alloc_or_nomem(tmp.a2, sizeof(double2) * (size_t)m[2] * k[1] * k[0])) != FSP_OK) return st;
+    const void *tab[3];
+    if ((st = roots_3(tmp, m, tab, s)) != FSP_OK) return st;
+    LinesArgs a{};
+    a.tw = tab[0], a.st = c[0].st, a.tpl = c[0].tpl, a.lgL = c[0].lgL;
+    a.in = tmp.g.p, a.out = tmp.a1.p;
+    a.in_pos = 1, a.in_line = m[0], a.in_batch = 0;
+    a.out_pos = 1, a.out_line = k[0], a.out_batch = 0;
+    a.n_in = m[0], a.n_out = k[0], a.nlines = m[1] * m[2], a.nbatch = 1;
+    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_CPLX, M_INV>(a, s)));
+    a.tw = tab[1], a.st = c[1].st, a.tpl = c[1].tpl, a.lgL = c[1].lgL;
+    a.in = tmp.a1.p, a.out = tmp.a2.p;
+    a.in_pos = k[0], a.in_line = 1, a.in_batch = (long long)m[1] * k[0];
+    a.out_pos = k[0], a.out_line = 1, a.out_batch = (long long)k[1] * k[0];
+    a.n_in = m[1], a.n_out = k[1], a.nlines = k[0], a.nbatch = m[2];
+    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_CPLX, M_INV>(a, s)));
+    a.tw = tab[2], a.st = c[2].st, a.tpl = c[2].tpl, a.lgL = c[2].lgL;
+    a.in = tmp.a2.p, a.out = t_dev;
+    a.in_pos = (long long)k[1] * k[0], a.in_line = 1, a.in_batch = k[0];
+    a.out_pos = (long long)k[1] * k[0], a.out_line = 1, a.out_batch = k[0];
+    a.n_in = m[2], a.n_out = k[2], a.nlines = k[0], a.nbatch = k[1];
+    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_REAL, M_INV>(a, s)));
     return FSP_OK;
 }
 
@@ -223,65 +290,80 @@ fsp_status enqueue_kernel_T(int N, double L, fsp_algo algo, double *t_dev, cudaS
     // FSP_VG, Sec. 2.3: G_L on the (4N)^3 grid, unnormalised inverse DFT per
     // axis, restricted to [0,N] per axis, real part, times (4Nh)^-3.
     const int n4 = 4 * N;
-    TileCfg cr, cc;
-    if (!make_cfg(n4, n4, sizeof(double2), 3, cr) || !make_cfg(n4, n4, sizeof(double2), 3, cc)) return FSP_EUNSUPPORTED;
     if ((st = alloc_or_nomem(tmp.g, sizeof(double2) * (size_t)n4 * n4 * n4)) != FSP_OK) return st;
-    if ((st = alloc_or_nomem(tmp.a1, sizeof(double2) * (size_t)n4 * n4 * k1)) != FSP_OK) return st;
-    if ((st = alloc_or_nomem(tmp.a2, sizeof(double2) * (size_t)n4 * k1 * k1)) != FSP_OK) return st;
-    if ((st = roots_f64(tmp.tw, n4, s)) != FSP_OK) return st;
     FSP_TRY_CUDA(launch_vg_sample_full(tmp.g.p, N, h, Lt, s));
-    LinesArgs a{};
-    a.tw = tmp.tw.p;
-    a.st = cr.st, a.tpl = cr.tpl, a.lgL = cr.lgL;
-    a.in = tmp.g.p, a.out = tmp.a1.p;
-    a.in_pos = 1, a.in_line = n4, a.in_batch = 0;
-    a.out_pos = 1, a.out_line = k1, a.out_batch = 0;
-    a.n_in = n4, a.n_out = k1, a.nlines = n4 * n4, a.nbatch = 1;
-    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_CPLX, M_INV>(a, s)));
-    a.tpl = cc.tpl, a.lgL = cc.lgL;
-    a.in = tmp.a1.p, a.out = tmp.a2.p;
-    a.in_pos = k1, a.in_line = 1, a.in_batch = (long long)n4 * k1;
-    a.out_pos = k1, a.out_line = 1, a.out_batch = (long long)k1 * k1;
-    a.n_in = n4, a.n_out = k1, a.nlines = k1, a.nbatch = n4;
-    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_CPLX, M_INV>(a, s)));
-    a.in = tmp.a2.p, a.out = t_dev;
-    a.in_pos = (long long)k1 * k1, a.in_line = 1, a.in_batch = k1;
-    a.out_pos = (long long)k1 * k1, a.out_line = 1, a.out_batch = k1;
-    a.n_in = n4, a.n_out = k1, a.nlines = k1, a.nbatch = k1;
-    FSP_TRY_CUDA((launch_lines<double, IN_CPLX, OUT_REAL, M_INV>(a, s)));
+    const int nn[3] = {N, N, N};
+    if ((st = enqueue_vg_inverse3(nn, t_dev, s, tmp)) != FSP_OK) return st;
     return cuda_status(launch_scale(t_dev, (long long)k1 * k1 * k1, scale, s));
 }
 
-// Spectrum of the mirrored kernel: DCT-I of length N+1 per axis on T in place
-// (the 2N DFT of a real sequence even about 0 and N), FP64.  For a field
-// kernel odd in axis `odd` (0 = x, 1 = y, 2 = z) that axis takes the DST-I
-// instead: the 2N DFT of the odd extension is -i times the result.
-fsp_status enqueue_trig_spectrum(int N, int odd, double *t_dev, cudaStream_t s, DevBuf &tw) {
-    const int k1 = N + 1, n = 2 * N;
-    TileCfg c;
-    if (!make_cfg(n, n, sizeof(double2), 3, c)) return FSP_EUNSUPPORTED;
-    fsp_status st = roots_f64(tw, n, s);
+// Real-space kernel T on a non-cubic box (n_x x n_y x n_z cells, spacings
+// h_x, h_y, h_z), (n_z+1)(n_y+1)(n_x+1) FP64 values into t_dev: the methods
+// of Sec. 2.2-2.4 per axis, the Vico-Greengard window alpha |(L_x, L_y, L_z)|.
+fsp_status enqueue_kernel_T3(const int *nn, const double *hh, fsp_algo algo, double *t_dev, cudaStream_t s, Temps &tmp) {
+    const long long tot = (long long)(nn[0] + 1) * (nn[1] + 1) * (nn[2] + 1);
+    if (algo == FSP_HE) return cuda_status(launch_he_T3(t_dev, nn, hh, s));
+    const double Lb[3] = {nn[0] * hh[0], nn[1] * hh[1], nn[2] * hh[2]};
+    const double Lt = kAlpha * std::sqrt(Lb[0] * Lb[0] + Lb[1] * Lb[1] + Lb[2] * Lb[2]);
+    const double scale = 1.0 / ((4.0 * nn[0] * hh[0]) * (4.0 * nn[1] * hh[1]) * (4.0 * nn[2] * hh[2]));
+    fsp_status st;
+    if (algo == FSP_VG_DCT) {
+        const size_t q = (size_t)(2 * nn[0] + 1) * (2 * nn[1] + 1) * (2 * nn[2] + 1);
+        if ((st = alloc_or_nomem(tmp.g, sizeof(double) * q)) != FSP_OK) return st;
+        FSP_TRY_CUDA(launch_vg_sample_octant3((double *)tmp.g.p, nn, hh, Lt, s));
+        if ((st = enqueue_octant_transform3(nn, -1, (double *)tmp.g.p, t_dev, s, tmp)) != FSP_OK) return st;
+    } else {
+        const size_t m = (size_t)(4 * nn[0]) * (4 * nn[1]) * (4 * nn[2]);
+        if ((st = alloc_or_nomem(tmp.g, sizeof(double2) * m)) != FSP_OK) return st;
+        FSP_TRY_CUDA(launch_vg_sample_full3(tmp.g.p, nn, hh, Lt, s));
+        if ((st = enqueue_vg_inverse3(nn, t_dev, s, tmp)) != FSP_OK) return st;
+    }
+    return cuda_status(launch_scale(t_dev, tot, scale, s));
+}
+
+// Spectrum of the mirrored kernel: DCT-I of length n_a+1 per axis on T in
+// place (the 2n_a DFT of a real sequence even about 0 and n_a), FP64.  For a
+// field kernel odd in axis `odd` (0 = x, 1 = y, 2 = z) that axis takes the
+// DST-I instead: the 2N DFT of the odd extension is -i times the result.
+fsp_status enqueue_trig_spectrum3(const int *nn, int odd, double *t_dev, cudaStream_t s, Temps &tmp) {
+    const int k[3] = {nn[0] + 1, nn[1] + 1, nn[2] + 1};
+    const int len[3] = {2 * nn[0], 2 * nn[1], 2 * nn[2]};
+    TileCfg c[3];
+    for (int a = 0; a < 3; ++a)
+        if (!make_cfg(len[a], len[a], sizeof(double2), 3, c[a])) return FSP_EUNSUPPORTED;
+    const void *tab[3];
+    fsp_status st = roots_3(tmp, len, tab, s);
     if (st != FSP_OK) return st;
     LinesArgs a{};
-    a.tw = tw.p, a.st = c.st, a.tpl = c.tpl, a.lgL = c.lgL;
     a.in = a.out = t_dev;
-    a.n_out = k1;
     // x: rows
-    a.in_pos = a.out_pos = 1, a.in_line = a.out_line = k1, a.in_batch = a.out_batch = 0;
-    a.nlines = k1 * k1, a.nbatch = 1;
+    a.tw = tab[0], a.st = c[0].st, a.tpl = c[0].tpl, a.lgL = c[0].lgL;
+    a.n_out = k[0];
+    a.in_pos = a.out_pos = 1, a.in_line = a.out_line = k[0], a.in_batch = a.out_batch = 0;
+    a.nlines = k[1] * k[2], a.nbatch = 1;
     FSP_TRY_CUDA(launch_trig(odd == 0, a, s));
     // y: columns, batch z
-    a.in_pos = a.out_pos = k1, a.in_line = a.out_line = 1, a.in_batch = a.out_batch = (long long)k1 * k1;
-    a.nlines = k1, a.nbatch = k1;
+    a.tw = tab[1], a.st = c[1].st, a.tpl = c[1].tpl, a.lgL = c[1].lgL;
+    a.n_out = k[1];
+    a.in_pos = a.out_pos = k[0], a.in_line = a.out_line = 1, a.in_batch = a.out_batch = (long long)k[1] * k[0];
+    a.nlines = k[0], a.nbatch = k[2];
     FSP_TRY_CUDA(launch_trig(odd == 1, a, s));
     // z: columns, batch y
-    a.in_pos = a.out_pos = (long long)k1 * k1, a.in_batch = a.out_batch = k1;
+    a.tw = tab[2], a.st = c[2].st, a.tpl = c[2].tpl, a.lgL = c[2].lgL;
+    a.n_out = k[2];
+    a.in_pos = a.out_pos = (long long)k[1] * k[0], a.in_batch = a.out_batch = k[0];
+    a.nlines = k[0], a.nbatch = k[1];
     FSP_TRY_CUDA(launch_trig(odd == 2, a, s));
     return FSP_OK;
 }
 
-fsp_status enqueue_dct_spectrum(int N, double *t_dev, cudaStream_t s, DevBuf &tw) {
-    return enqueue_trig_spectrum(N, -1, t_dev, s, tw);
+fsp_status enqueue_trig_spectrum(int N, int odd, double *t_dev, cudaStream_t s, Temps &tmp) {
+    const int nn[3] = {N, N, N};
+    return enqueue_trig_spectrum3(nn, odd, t_dev, s, tmp);
+}
+
+fsp_status enqueue_dct_spectrum(int N, double *t_dev, cudaStream_t s, Temps &tmp) {
+    return enqueue_trig_spectrum(N, -1, t_dev, s, tmp);
 }
 
 // Field kernel F_a[m] = -dG/dx_a (m h), m in [0,N]^3, into f_dev (FP64), for
@@ -336,6 +418,14 @@ struct fsp_plan {
     // field solves (fsp_plan_field_init): the spectra of F_x, F_y, F_z and the
     // third workspace the out-of-place P3 of each component writes
     void *SF[3] = {}, *W3 = nullptr;
+    // a non-cubic box (fsp_plan_create_aniso): n3 cells and h3 spacings per
+    // axis, the generic engine with its own tiles and roots for the y (2 n_y)
+    // and z (2 n_z) lines; rows use tw_n / tw_2n of n_x
+    bool aniso = false;
+    int n3[3] = {};
+    double h3[3] = {};
+    TileCfg colz;
+    void *tw_y = nullptr, *tw_z = nullptr;
     cudaEvent_t ev[6] = {};
     bool timing = false;
     size_t bytes = 0;
@@ -349,9 +439,14 @@ bool plan_live(const fsp_plan *p) {
     return p && g_plans.count(p) && p->magic == kMagic;
 }
 
+// grid points of a plan's source / result
+size_t plan_points(const fsp_plan *p) {
+    return p->aniso ? (size_t)p->n3[0] * p->n3[1] * p->n3[2] : (size_t)p->N * p->N * p->N;
+}
+
 void plan_free(fsp_plan *p) {
     for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi, p->pipe_rho[0], p->pipe_rho[1],
-                    p->pipe_phi[0], p->pipe_phi[1], p->SF[0], p->SF[1], p->SF[2], p->W3})
+                    p->pipe_phi[0], p->pipe_phi[1], p->SF[0], p->SF[1], p->SF[2], p->W3, p->tw_y, p->tw_z})
         if (q) cudaFree(q);
     for (cudaStream_t q : {p->pipe_h2d, p->pipe_d2h})
         if (q) cudaStreamDestroy(q);
@@ -517,8 +612,53 @@ cudaError_t enqueue_field(const fsp_plan *p, const void *rho, void *const out[4]
                                : enqueue_field_generic<float>(p, rho, out, s);
 }
 
+// Sec. 2.2 steps 1-5 on a non-cubic box, generic engine: P1 rows of n_x, P2
+// y lines of 2 n_y (batch z), P3 z lines of 2 n_z (batch k_y; S folded at n_z
+// in z and n_y in k_y), P4, P5.  W1 = n_z n_y P, W2 = n_z 2 n_y P complex.
+template <typename T>
+cudaError_t enqueue_solve_aniso(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
+    const int nx = p->n3[0], ny = p->n3[1], nz = p->n3[2];
+    const long long P = p->P;
+    cudaError_t e;
+    auto mark = [&](int i) { return p->timing ? cudaEventRecord(p->ev[i], s) : cudaSuccess; };
+    if ((e = mark(0)) != cudaSuccess) return e;
+    RowsArgs r{};
+    r.x = rho, r.c = W1, r.x_row = nx, r.c_row = P, r.N = nx, r.nrows = ny * nz;
+    r.lgL = p->row.lgL, r.tpl = p->row.tpl, r.st = p->row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    if ((e = launch_r2c_rows<T>(r, s)) != cudaSuccess) return e;
+    if ((e = mark(1)) != cudaSuccess) return e;
+    LinesArgs a{};
+    a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_y;
+    a.in = W1, a.out = W2;
+    a.in_pos = P, a.in_line = 1, a.in_batch = (long long)ny * P;
+    a.out_pos = P, a.out_line = 1, a.out_batch = 2LL * ny * P;
+    a.n_in = ny, a.n_out = 2 * ny, a.nlines = nx + 1, a.nbatch = nz;
+    if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD>(a, s)) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
+    a.st = p->colz.st, a.tpl = p->colz.tpl, a.lgL = p->colz.lgL, a.tw = p->tw_z;
+    a.in = a.out = W2;
+    a.in_pos = a.out_pos = 2LL * ny * P, a.in_batch = a.out_batch = P;
+    a.n_in = nz, a.n_out = nz, a.nbatch = 2 * ny;
+    a.S = p->S, a.s_pos = (long long)(ny + 1) * P, a.s_batch = P, a.half = nz, a.half_b = ny;
+    if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD_MUL_INV>(a, s)) != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
+    a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_y;
+    a.in = W2, a.out = W1;
+    a.in_pos = P, a.in_batch = 2LL * ny * P;
+    a.out_pos = P, a.out_batch = (long long)ny * P;
+    a.n_in = 2 * ny, a.n_out = ny, a.nbatch = nz;
+    if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_INV>(a, s)) != cudaSuccess) return e;
+    if ((e = mark(4)) != cudaSuccess) return e;
+    r.x = phi;
+    if ((e = launch_c2r_rows<T>(r, s)) != cudaSuccess) return e;
+    return mark(5);
+}
+
 // One solve of plan p with the given workspace (W1: N*N*P, W2: 2*N*N*P complex).
 cudaError_t enqueue_solve_ws(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
+    if (p->aniso)
+        return p->dtype == FSP_F64 ? enqueue_solve_aniso<double>(p, rho, phi, W1, W2, s)
+                                   : enqueue_solve_aniso<float>(p, rho, phi, W1, W2, s);
     if (p->dtype == FSP_F64_DF) return enqueue_solve_fast<df>(p, rho, phi, W1, W2, s);
     if (p->fast)
         return p->dtype == FSP_F64 ? enqueue_solve_fast<double>(p, rho, phi, W1, W2, s)
@@ -613,8 +753,8 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     if (e != cudaSuccess) return fail(FSP_ECUDA);
 
     {  // plan-time spectrum, FP64 throughout
-        Temps tmp;
-        DevBuf Td, tw;
+        Temps tmp, tw;
+        DevBuf Td;
         if ((st = alloc_or_nomem(Td, sizeof(double) * k1 * k1 * k1)) != FSP_OK) return fail(st);
         if ((st = enqueue_kernel_T(N, L, algo, (double *)Td.p, s, tmp)) != FSP_OK) return fail(st);
         if ((st = enqueue_dct_spectrum(N, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
@@ -644,6 +784,103 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
     return plan_create_impl(out, N, L, h, algo, dtype, stream, true);
 }
 
+fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double hx, double hy, double hz,
+                                 fsp_algo algo, fsp_dtype dtype, fsp_stream stream) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    const int nn[3] = {nx, ny, nz};
+    const double hh[3] = {hx, hy, hz};
+    if (algo != FSP_HE && algo != FSP_VG && algo != FSP_VG_DCT) return FSP_EINVAL;
+    if (dtype != FSP_F64 && dtype != FSP_F32_MIXED && dtype != FSP_F64_DF) return FSP_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        if (nn[a] < 2 || !(hh[a] > 0.0) || !std::isfinite(hh[a])) return FSP_EINVAL;
+        if (nn[a] > kMaxN || !is_235_smooth(2LL * nn[a])) return FSP_EUNSUPPORTED;
+        if (algo == FSP_VG && !is_235_smooth(4LL * nn[a])) return FSP_EUNSUPPORTED;
+    }
+    if (nx == ny && ny == nz && hx == hy && hy == hz)  // a cube: the cubic plan and its kernels
+        return plan_create_impl(out, nx, nx * hx, hx, algo, dtype, stream, true);
+    if (dtype == FSP_F64_DF) return FSP_EUNSUPPORTED;  // double-float: specialised cubic kernels only
+    if (algo != FSP_HE) {
+        // the (4 n_a h_a) periodisation of the truncated kernel must not reach
+        // the box: 3 min_a L_a >= L_t = alpha |(L_x, L_y, L_z)|
+        const double Lb[3] = {nx * hx, ny * hy, nz * hz};
+        const double Lt = kAlpha * std::sqrt(Lb[0] * Lb[0] + Lb[1] * Lb[1] + Lb[2] * Lb[2]);
+        if (3.0 * std::min(Lb[0], std::min(Lb[1], Lb[2])) < Lt) return FSP_EUNSUPPORTED;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    fsp_plan *p = new fsp_plan();
+    p->aniso = true;
+    for (int a = 0; a < 3; ++a) p->n3[a] = nn[a], p->h3[a] = hh[a];
+    p->N = nx, p->L = nx * hx, p->h = hx, p->algo = algo, p->dtype = dtype;
+    p->rsize = dtype == FSP_F32_MIXED ? 4 : 8;
+    p->P = ((nx + 1) + 15) / 16 * 16;
+    const size_t csize = 2 * p->rsize;
+    const int lg = dtype == FSP_F32_MIXED ? 4 : 3;
+    if (!make_cfg(nx, nx + 1, csize, lg, p->row) || !make_cfg(2 * ny, 2 * ny, csize, lg, p->col) ||
+        !make_cfg(2 * nz, 2 * nz, csize, lg, p->colz)) {
+        delete p;
+        return FSP_EUNSUPPORTED;
+    }
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return FSP_ECUDA;
+    }
+    auto fail = [&](fsp_status e) {
+        cudaStreamSynchronize(s);
+        plan_free(p);
+        return e;
+    };
+    const size_t sbytes = (size_t)(nz + 1) * (ny + 1) * p->P * p->rsize;
+    const size_t w1 = (size_t)nz * ny * p->P * csize, w2 = 2 * w1;
+    fsp_status st;
+    DevBuf bS, bW1, bW2, b1, b2, by, bz;
+    if ((st = alloc_or_nomem(bS, sbytes)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(bW1, w1)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(bW2, w2)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(b1, csize * nx)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(b2, csize * 2 * nx)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(by, csize * 2 * ny)) != FSP_OK) return fail(st);
+    if ((st = alloc_or_nomem(bz, csize * 2 * nz)) != FSP_OK) return fail(st);
+    p->S = bS.release(), p->W1 = bW1.release(), p->W2 = bW2.release();
+    p->tw_n = b1.release(), p->tw_2n = b2.release(), p->tw_y = by.release(), p->tw_z = bz.release();
+    p->bytes = sbytes + w1 + w2 + csize * (3 * nx + 2 * ny + 2 * nz);
+    cudaError_t e;
+    if (dtype == FSP_F64) {
+        e = launch_roots<double>(p->tw_n, nx, s);
+        if (e == cudaSuccess) e = launch_roots<double>(p->tw_2n, 2 * nx, s);
+        if (e == cudaSuccess) e = launch_roots<double>(p->tw_y, 2 * ny, s);
+        if (e == cudaSuccess) e = launch_roots<double>(p->tw_z, 2 * nz, s);
+    } else {
+        e = launch_roots<float>(p->tw_n, nx, s);
+        if (e == cudaSuccess) e = launch_roots<float>(p->tw_2n, 2 * nx, s);
+        if (e == cudaSuccess) e = launch_roots<float>(p->tw_y, 2 * ny, s);
+        if (e == cudaSuccess) e = launch_roots<float>(p->tw_z, 2 * nz, s);
+    }
+    if (e != cudaSuccess) return fail(FSP_ECUDA);
+    {  // plan-time spectrum, FP64 throughout
+        Temps tmp, tw;
+        DevBuf Td;
+        const long long rows = (long long)(ny + 1) * (nz + 1);
+        if ((st = alloc_or_nomem(Td, sizeof(double) * (size_t)(nx + 1) * rows)) != FSP_OK) return fail(st);
+        if ((st = enqueue_kernel_T3(nn, hh, algo, (double *)Td.p, s, tmp)) != FSP_OK) return fail(st);
+        if ((st = enqueue_trig_spectrum3(nn, -1, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
+        const double scale = hx * hy * hz / ((2.0 * nx) * (2.0 * ny) * (2.0 * nz));
+        e = dtype == FSP_F64 ? launch_store_S3<double>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s)
+                             : launch_store_S3<float>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s);
+        if (e != cudaSuccess) return fail(FSP_ECUDA);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FSP_ECUDA);
+    }
+    p->precompute_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    p->magic = kMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_plans.insert(p);
+    }
+    *out = p;
+    return FSP_OK;
+}
+
 fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stream) {
     if (!plan_live(plan)) return FSP_EINVAL;
     if (!rho || !phi || !aligned16(rho) || !aligned16(phi)) return FSP_EINVAL;
@@ -659,6 +896,7 @@ fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stre
 fsp_status fsp_plan_field_init(fsp_plan *plan, fsp_stream stream) {
     if (!plan_live(plan)) return FSP_EINVAL;
     if (!plan->W1) return FSP_EINVAL;
+    if (plan->aniso) return FSP_EUNSUPPORTED;  // field solves: cubic boxes
     if (plan->W3) return FSP_OK;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
@@ -680,8 +918,8 @@ fsp_status fsp_plan_field_init(fsp_plan *plan, fsp_stream stream) {
         // plan-time field spectrum S_a = h^3 / (2N)^3 * DST/DCT of F_a, FP64,
         // rounded to the plan's type; each component's temporaries live
         // until its work has finished
-        Temps tmp;
-        DevBuf Fd, tw;
+        Temps tmp, tw;
+        DevBuf Fd;
         if ((st = alloc_or_nomem(Fd, sizeof(double) * k1 * k1 * k1)) != FSP_OK) return st;
         if ((st = enqueue_field_kernel(N, plan->L, plan->algo, axis, (double *)Fd.p, s, tmp)) != FSP_OK) {
             cudaStreamSynchronize(s);
@@ -724,7 +962,7 @@ fsp_status fsp_solve_host(fsp_plan *plan, const void *rho_host, void *phi_host, 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
     if (dev != plan->device) return FSP_EINVAL;
-    const size_t bytes = (size_t)plan->N * plan->N * plan->N * plan->rsize;
+    const size_t bytes = plan_points(plan) * plan->rsize;
     if (!plan->stage_rho) {
         DevBuf a, b;
         fsp_status st;
@@ -752,7 +990,7 @@ fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void
     if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
     if (dev != plan->device) return FSP_EINVAL;
     if (count == 0) return FSP_OK;
-    const size_t bytes = (size_t)plan->N * plan->N * plan->N * plan->rsize;
+    const size_t bytes = plan_points(plan) * plan->rsize;
     if (!plan->pipe_h2d) {  // first use: staging pairs, copy streams, events
         DevBuf a0, a1, b0, b1;
         fsp_status st;
@@ -846,6 +1084,18 @@ double fsp_plan_precompute_ms(const fsp_plan *plan) { return plan_live(plan) ? p
 
 fsp_status fsp_plan_spectrum(const fsp_plan *plan, double *s_host) {
     if (!plan_live(plan) || !s_host) return FSP_EINVAL;
+    if (plan->aniso) {
+        const int kx = plan->n3[0] + 1;
+        const long long rows = (long long)(plan->n3[1] + 1) * (plan->n3[2] + 1);
+        const size_t tot = (size_t)kx * rows;
+        DevBuf d;
+        fsp_status st = alloc_or_nomem(d, sizeof(double) * tot);
+        if (st != FSP_OK) return st;
+        cudaError_t e = plan->dtype == FSP_F64 ? launch_load_S3<double>(plan->S, (double *)d.p, kx, rows, plan->P, 0)
+                                               : launch_load_S3<float>(plan->S, (double *)d.p, kx, rows, plan->P, 0);
+        if (e != cudaSuccess) return FSP_ECUDA;
+        return cuda_status(cudaMemcpy(s_host, d.p, sizeof(double) * tot, cudaMemcpyDeviceToHost));
+    }
     const size_t k1 = plan->N + 1, tot = k1 * k1 * k1;
     DevBuf d;
     fsp_status st = alloc_or_nomem(d, sizeof(double) * tot);
@@ -1100,6 +1350,7 @@ extern "C" fsp_status fsp_batch_create(fsp_batch **out, fsp_plan *const *plans, 
         if (!plan_live(plans[i]) || !seen.insert(plans[i]).second) return FSP_EINVAL;  // distinct live plans
         if (plans[i]->dtype != plans[0]->dtype || plans[i]->device != plans[0]->device) return FSP_EINVAL;
         if (plans[i]->dtype == FSP_F64_DF) return FSP_EUNSUPPORTED;  // batches use the generic engine
+        if (plans[i]->aniso) return FSP_EUNSUPPORTED;                // and cubic boxes
         if (!rho[i] || !phi[i] || !aligned16(rho[i]) || !aligned16(phi[i])) return FSP_EINVAL;
     }
     int dev = -1;

@@ -93,29 +93,65 @@ __global__ void k_vg_sample_octant_grad(double *g, int M, double dk, double Lt, 
     }
 }
 
+// Non-cubic boxes (n_x x n_y x n_z cells, spacings h_x, h_y, h_z).
+// T[m] = 1/(4 pi |(m_x h_x, m_y h_y, m_z h_z)|), T[0] = 1/(4 pi); m in the
+// (n_x+1, n_y+1, n_z+1) octant, x fastest.
+__global__ void k_he_T3(double *T, int kx, int ky, int kz, double hx, double hy, double hz) {
+    const long long tot = (long long)kx * ky * kz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % kx), y = (int)((i / kx) % ky), z = (int)(i / ((long long)kx * ky));
+        const double dx = x * hx, dy = y * hy, dz = z * hz;
+        T[i] = (x | y | z) ? inv4pi() / sqrt(dx * dx + dy * dy + dz * dz) : inv4pi();
+    }
+}
+
+// g[j] = G_L(|(dk_x j_x, dk_y j_y, dk_z j_z)|) for j in the (q_x, q_y, q_z)
+// octant, q_a = 2 n_a + 1.
+__global__ void k_vg_sample_octant3(double *g, int qx, int qy, int qz, double dkx, double dky, double dkz, double Lt) {
+    const long long tot = (long long)qx * qy * qz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % qx), y = (int)((i / qx) % qy), z = (int)(i / ((long long)qx * qy));
+        const double kx = dkx * x, ky = dky * y, kz = dkz * z;
+        g[i] = green_vico_hat(sqrt(kx * kx + ky * ky + kz * kz), Lt);
+    }
+}
+
+// g[s] = G_L(|k|) on the (4n_x, 4n_y, 4n_z) grid, storage index s holding
+// frequency j_a = s_a for s_a < 2 n_a and s_a - 4 n_a otherwise.
+__global__ void k_vg_sample_full3(double2 *g, int mx, int my, int mz, double dkx, double dky, double dkz, double Lt) {
+    const long long tot = (long long)mx * my * mz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(i % mx), y = (int)((i / mx) % my), z = (int)(i / ((long long)mx * my));
+        x = x < mx / 2 ? x : x - mx;
+        y = y < my / 2 ? y : y - my;
+        z = z < mz / 2 ? z : z - mz;
+        const double kx = dkx * x, ky = dky * y, kz = dkz * z;
+        g[i] = double2{green_vico_hat(sqrt(kx * kx + ky * ky + kz * kz), Lt), 0.0};
+    }
+}
+
 __global__ void k_scale(double *a, long long n, double s) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] *= s;
 }
 
-// S[qz][qy][qx] (row pitch P) = scale * Sd[qz][qy][qx] rounded to T.
-template <typename T> __global__ void k_store_S(const double *Sd, T *S, int N, int P, double scale) {
-    const int k1 = N + 1;
-    const long long tot = (long long)k1 * k1 * k1;
+// S[qz][qy][qx] (row pitch P) = scale * Sd[qz][qy][qx] rounded to T; rows of
+// kx values, `rows` = (n_z+1)(n_y+1) of them.
+template <typename T> __global__ void k_store_S(const double *Sd, T *S, int kx, long long rows, int P, double scale) {
+    const long long tot = (long long)kx * rows;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % k1);
-        const long long row = i / k1;  // qz*(N+1) + qy
+        const int x = (int)(i % kx);
+        const long long row = i / kx;  // qz*(n_y+1) + qy
         S[row * P + x] = (T)(scale * Sd[i]);
     }
 }
 
-// S (pitch P, type T) -> dense (N+1)^3 doubles
-template <typename T> __global__ void k_load_S(const T *S, double *Sd, int N, int P) {
-    const int k1 = N + 1;
-    const long long tot = (long long)k1 * k1 * k1;
+// S (pitch P, type T) -> dense rows of kx doubles
+template <typename T> __global__ void k_load_S(const T *S, double *Sd, int kx, long long rows, int P) {
+    const long long tot = (long long)kx * rows;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % k1);
-        Sd[i] = (double)S[(i / k1) * P + x];
+        const int x = (int)(i % kx);
+        Sd[i] = (double)S[(i / kx) * P + x];
     }
 }
 
@@ -167,15 +203,45 @@ cudaError_t launch_scale(double *a, long long n, double sc, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_store_S(const double *Sd, void *S, int N, int P, double scale, cudaStream_t s) {
-    const long long tot = (long long)(N + 1) * (N + 1) * (N + 1);
-    k_store_S<T><<<grid_for(tot), 256, 0, s>>>(Sd, reinterpret_cast<T *>(S), N, P, scale);
+template <typename T>
+cudaError_t launch_store_S3(const double *Sd, void *S, int kx, long long rows, int P, double scale, cudaStream_t s) {
+    k_store_S<T><<<grid_for((long long)kx * rows), 256, 0, s>>>(Sd, reinterpret_cast<T *>(S), kx, rows, P, scale);
     return cudaGetLastError();
 }
 
+template <typename T> cudaError_t launch_load_S3(const void *S, double *Sd, int kx, long long rows, int P, cudaStream_t s) {
+    k_load_S<T><<<grid_for((long long)kx * rows), 256, 0, s>>>(reinterpret_cast<const T *>(S), Sd, kx, rows, P);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_store_S(const double *Sd, void *S, int N, int P, double scale, cudaStream_t s) {
+    return launch_store_S3<T>(Sd, S, N + 1, (long long)(N + 1) * (N + 1), P, scale, s);
+}
+
 template <typename T> cudaError_t launch_load_S(const void *S, double *Sd, int N, int P, cudaStream_t s) {
-    const long long tot = (long long)(N + 1) * (N + 1) * (N + 1);
-    k_load_S<T><<<grid_for(tot), 256, 0, s>>>(reinterpret_cast<const T *>(S), Sd, N, P);
+    return launch_load_S3<T>(S, Sd, N + 1, (long long)(N + 1) * (N + 1), P, s);
+}
+
+cudaError_t launch_he_T3(double *T, const int *n, const double *h, cudaStream_t s) {
+    const long long tot = (long long)(n[0] + 1) * (n[1] + 1) * (n[2] + 1);
+    k_he_T3<<<grid_for(tot), 256, 0, s>>>(T, n[0] + 1, n[1] + 1, n[2] + 1, h[0], h[1], h[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vg_sample_octant3(double *g, const int *n, const double *h, double Lt, cudaStream_t s) {
+    const int q[3] = {2 * n[0] + 1, 2 * n[1] + 1, 2 * n[2] + 1};
+    double dk[3];
+    for (int a = 0; a < 3; ++a) dk[a] = 6.283185307179586476925286766559 / (4.0 * n[a] * h[a]);
+    k_vg_sample_octant3<<<grid_for((long long)q[0] * q[1] * q[2]), 256, 0, s>>>(g, q[0], q[1], q[2], dk[0], dk[1], dk[2], Lt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vg_sample_full3(void *g, const int *n, const double *h, double Lt, cudaStream_t s) {
+    const int m[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
+    double dk[3];
+    for (int a = 0; a < 3; ++a) dk[a] = 6.283185307179586476925286766559 / (4.0 * n[a] * h[a]);
+    k_vg_sample_full3<<<grid_for((long long)m[0] * m[1] * m[2]), 256, 0, s>>>(reinterpret_cast<double2 *>(g), m[0], m[1],
+                                                                                m[2], dk[0], dk[1], dk[2], Lt);
     return cudaGetLastError();
 }
 
@@ -185,5 +251,9 @@ template cudaError_t launch_load_S<df>(const void *, double *, int, int, cudaStr
 template cudaError_t launch_store_S<double>(const double *, void *, int, int, double, cudaStream_t);
 template cudaError_t launch_load_S<float>(const void *, double *, int, int, cudaStream_t);
 template cudaError_t launch_load_S<double>(const void *, double *, int, int, cudaStream_t);
+template cudaError_t launch_store_S3<float>(const double *, void *, int, long long, int, double, cudaStream_t);
+template cudaError_t launch_store_S3<double>(const double *, void *, int, long long, int, double, cudaStream_t);
+template cudaError_t launch_load_S3<float>(const void *, double *, int, long long, int, cudaStream_t);
+template cudaError_t launch_load_S3<double>(const void *, double *, int, long long, int, cudaStream_t);
 
 }  // namespace fsp

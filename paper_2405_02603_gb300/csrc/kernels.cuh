@@ -34,10 +34,12 @@ struct LinesArgs {
     Stages st;   // transform length st.n
     const void *tw;  // forward roots exp(-2 pi i e / n), e in [0,n)
     // M_FWD_MUL_INV: multiply position p of line c in batch b by the real
-    // S[fold(p)*s_pos + fold(b)*s_batch + c], fold(k) = min(k, 2*half - k)
+    // S[fold(p)*s_pos + fold_b(b)*s_batch + c], fold(k) = min(k, 2*half - k),
+    // fold_b the same with half_b (0: half_b = half; a non-cubic box folds k_y
+    // at n_y and z at n_z)
     const void *S;
     long long s_pos, s_batch;
-    int half;
+    int half, half_b;
     // 0: S is even in every index (the potential).  1, 2, 3: S holds a
     // spectrum odd in the position, batch or line index (a field component):
     // the multiplier is -i S[fold], negated where that index exceeds half.

@@ -94,10 +94,11 @@ __device__ __forceinline__ void lines_tile(const LinesArgs &a, int bx, long long
     if (MODE == M_FWD_MUL_INV) {
         const T *S = reinterpret_cast<const T *>(a.S);
         const int h2 = 2 * a.half;
-        const int fy = (int)b <= a.half ? (int)b : h2 - (int)b;
+        const int hb = a.half_b ? a.half_b : a.half;
+        const int fy = (int)b <= hb ? (int)b : 2 * hb - (int)b;
         const int cnt = L * n;
         const int odd = a.odd;
-        const T sb = odd == 2 && (int)b > a.half ? T(-1) : T(1);
+        const T sb = odd == 2 && (int)b > hb ? T(-1) : T(1);
         for (int idx = tid; idx < cnt; idx += nth) {
             const int ll = idx & lmask, p = idx >> a.lgL;
             if (line0 + ll < a.nlines) {

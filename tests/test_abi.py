@@ -48,6 +48,24 @@ def test_plan_create_validation_needs_no_device(L):
     assert L.fsp_plan_create(None, 8, 1.0, 0.125, 0, 0, None) == 1
 
 
+def test_aniso_plan_validation_needs_no_device(L):
+    p = ctypes.c_void_p()
+    c = L.fsp_plan_create_aniso
+    assert c(None, 8, 8, 16, 0.1, 0.1, 0.1, 0, 0, None) == 1
+    # sizes, spacings, method, dtype
+    for args in [(1, 8, 8, 0.1, 0.1, 0.1, 0, 0), (8, 8, 8, 0.1, -0.1, 0.1, 0, 0), (8, 8, 8, 0.1, 0.1, float("nan"), 0, 0),
+                 (8, 8, 8, 0.1, 0.1, 0.1, 7, 0), (8, 8, 8, 0.1, 0.1, 0.1, 0, 9)]:
+        assert c(ctypes.byref(p), *args, None) == 1, args
+        assert not p.value
+    # 2 n_a not smooth, n_a too large, 4 n_a not smooth for VG
+    assert c(ctypes.byref(p), 8, 7, 8, 0.1, 0.1, 0.1, 0, 0, None) == 2
+    assert c(ctypes.byref(p), 8, 8, 2048, 0.1, 0.1, 0.1, 0, 0, None) == 2
+    # the Vico-Greengard window beyond 3 min L_a (1 x 1 x 2.5 box), double-float on a non-cube
+    assert c(ctypes.byref(p), 16, 16, 40, 1.0 / 16, 1.0 / 16, 1.0 / 16, 1, 0, None) == 2
+    assert c(ctypes.byref(p), 16, 16, 40, 1.0 / 16, 1.0 / 16, 1.0 / 16, 2, 0, None) == 2
+    assert c(ctypes.byref(p), 16, 16, 32, 1.0 / 16, 1.0 / 16, 1.0 / 16, 0, 2, None) == 2
+
+
 def test_unknown_plan_is_rejected(L):
     fake = ctypes.c_void_p(0x1000)
     assert L.fsp_solve(fake, fake, fake, None) == 1

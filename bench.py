@@ -303,6 +303,68 @@ def field_leg(fsp, N, L, algo, K, W, world):
     return out
 
 
+def pass_bytes3(n, c, r):
+    """pass_bytes on a non-cubic box of n = (n_x, n_y, n_z) cells."""
+    a = n[2] * n[1] * (n[0] + 1) * c
+    pts = n[0] * n[1] * n[2]
+    return [pts * r + a, 3 * a, 4 * a + (n[0] + 1) * (n[1] + 1) * (n[2] + 1) * r, 3 * a, a + pts * r]
+
+
+def noncubic_leg(fsp, n, L, K, W, world, hbm, hbm_kind):
+    """The 1 x 1 x 2 box of the paper's weak-scaling runs (Sec. 3.2) at
+    n = (n_x, n_y, n_z), VG-DCT (the memory-reduced form: the (4n)^3 grid of
+    plain VG would not fit), FP32-mixed and FP64, generic engine; per-pass
+    events give the dominant pass's roofline."""
+    import torch
+    out = {}
+    for dtype, c, r in (("f32", 8, 4), ("f64", 16, 8)):
+        plan = fsp.Plan(n, L, "vg_dct", dtype)
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        srcs = [torch.from_numpy(I.gaussian_mixture3(n, L, seed=2405 + i).astype(np.float32)).to(tdt).cuda()
+                for i in range(2)]
+        dsts = [torch.empty_like(x) for x in srcs]
+        k = K if dtype == "f32" else max(5, K // 8)
+        stream = torch.cuda.current_stream()
+        for i in range(W):
+            plan.solve_into(srcs[i % 2], dsts[i % 2])
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(k)]
+        for row in ev:
+            for e in row:
+                e.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(k):
+            plan.set_timing(ev[i])
+            plan.solve_into(srcs[i % 2], dsts[i % 2])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        plan.set_timing(None)
+        per_pass = np.array([[ev[i][j].elapsed_time(ev[i][j + 1]) for j in range(5)] for i in range(k)])
+        value, tmax = replica_value(k, t0.elapsed_time(t1), world)
+        pb = pass_bytes3(n, c, r)
+        kk = int(np.argmax(per_pass.sum(axis=0)))
+        dur = float(per_pass[:, kk].mean()) * 1e-3
+        t = tmax / k
+        out[dtype] = {"value": round(value, 2), "unit": "solves/s", "steps": k, "ms_per_step": round(t, 4),
+                      "hbm_gbs_solve": round(sum(pb) / (t * 1e-3) / 1e9, 1),
+                      "roofline": {"bound": "hbm", "kernel": PASS_NAMES[kk].split(" (")[0] + " (generic engine)",
+                                   "achieved": round(pb[kk] / dur / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                                   "frac": round(pb[kk] / dur / 1e9 / hbm, 4),
+                                   "peak_kind": hbm_kind + " copy bandwidth",
+                                   "pass_ms": [round(float(x), 4) for x in per_pass.mean(axis=0)]},
+                      "precompute_ms": round(plan.precompute_ms, 1), "gpu_launches": 5 * k}
+        plan.close()
+        del srcs, dsts
+        torch.cuda.empty_cache()
+    out["config"] = {"n": list(n), "L": list(L), "algo": "vg_dct",
+                     "workload": "VG-DCT solve on the 1 x 1 x 2 box of the weak-scaling runs (Sec. 3.2), "
+                                 "%d x %d x %d cells" % tuple(n)}
+    return out
+
+
 def roofline(N, c, r, leg, dtype, hbm, hbm_kind):
     pb = pass_bytes(N, c, r)
     share = leg["per_pass"].sum(axis=0)
@@ -595,6 +657,7 @@ def main():
     out["field"] = field_leg(fsp, N, L, args.algo, max(10, K // 4), W, world)
     out["field"]["roofline"].update({"peak": hbm, "frac": round(out["field"]["roofline"]["achieved"] / hbm, 4),
                                      "peak_kind": hbm_kind + " copy bandwidth"})
+    out["noncubic"] = noncubic_leg(fsp, (N, N, 2 * N), (1.0, 1.0, 2.0), max(10, K // 10), W, world, hbm, hbm_kind)
     if not args.no_systems:
         out["batched"] = {"f32": batch_leg(fsp, "f32"), "f64": batch_leg(fsp, "f64")}
         out["serving"] = serving_leg(fsp)

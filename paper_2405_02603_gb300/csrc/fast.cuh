@@ -71,6 +71,21 @@ template <typename T> __device__ __forceinline__ void store_pair(typename io_of<
         reinterpret_cast<cx_t<T> *>(row)[m] = v;
 }
 
+// loads that bypass L1 (ld.global.cg): streamed data and spectrum values
+// are read once per CTA, so they should not evict the twiddle table from L1
+__device__ __forceinline__ float2 ldcg_c(const float2 *p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldcg_c(const double2 *p) { return __ldcg(p); }
+__device__ __forceinline__ cdf ldcg_c(const cdf *p) {
+    const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+    return cdf{df(q.x, q.y, 0), df(q.z, q.w, 0)};
+}
+__device__ __forceinline__ float ldcg_r(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg_r(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ df ldcg_r(const df *p) {
+    const float2 q = __ldcg(reinterpret_cast<const float2 *>(p));
+    return df(q.x, q.y, 0);
+}
+
 template <int I, int E> struct StaticFor {
     template <class F> static __device__ __forceinline__ void run(F &&f) {
         if constexpr (I < E) {
@@ -187,14 +202,20 @@ template <typename T, int D> struct RD {
 
 // ---------------------------------------------------------------- stages --
 // n: transform length; V: values per thread; L: lines per CTA (pitch L+1).
-template <typename T, int D, int n, int V, int L> struct Stg {
+// TWS: the roots table is in shared memory (generic loads) rather than read
+// through the read-only global path.
+template <typename T, int D, int n, int V, int L, bool TWS = false> struct Stg {
     using C = cx_t<T>;
     static constexpr int TPL = n / V;
     static constexpr int LD = L + 1;
 
     // exp(D 2 pi i e / n) from the forward roots table
     static __device__ __forceinline__ C twid(const C *__restrict__ tw, int e) {
-        C w = ldg_c(tw + e);
+        C w;
+        if constexpr (TWS)
+            w = tw[e];
+        else
+            w = ldg_c(tw + e);
         if (D > 0) w.y = -w.y;
         return w;
     }
@@ -238,9 +259,9 @@ template <typename T, int D, int n, int V, int L> struct Stg {
 // registers: exchange through shared memory, compute; leaves the last
 // stage's outputs in registers.  `first_sync` is needed when shared memory
 // was read just before (the caller's previous stage loaded from it).
-template <typename T, int D, int n, int V, int L, int R1, int R2, int R3, bool HO_LAST>
+template <typename T, int D, int n, int V, int L, int R1, int R2, int R3, bool HO_LAST, bool TWS = false>
 __device__ __forceinline__ void run_rest(cx_t<T> *v, cx_t<T> *buf, int t, int l, const cx_t<T> *tw, bool first_sync) {
-    using S = Stg<T, D, n, V, L>;
+    using S = Stg<T, D, n, V, L, TWS>;
     if (first_sync) __syncthreads();
     S::template store_out<R1, 1>(buf, v, t, l);
     __syncthreads();
@@ -284,6 +305,19 @@ template <int n, int MODE> struct ColGeo {
     static constexpr long long S_POS = (long long)(N + 1) * P, S_BATCH = P;
 };
 
+// Per (type, pass) choices, each measured on the GB300 at N = 256:
+//   PF:  prefetch the thread's spectrum values into L1 before the forward
+//        transform (P3: their latency overlaps the transform; FP32 P3 -5 %).
+//   TWS: roots table in shared memory: double-float P3 -11 % and P2 -2 %,
+//        the FP32 field P3 (COL_FMO) faster too; FP32 P3 of the potential
+//        (COL_FMI), native FP64 and every P4 are slower or unchanged with it.
+template <typename T, int MODE> struct ColOpt {
+    static constexpr bool ZL = MODE == COL_FMI || MODE == COL_FMO;
+    static constexpr bool DF = std::is_same<T, df>::value;
+    static constexpr bool PF = ZL && !DF;
+    static constexpr bool TWS = (DF && MODE != COL_INV) || (MODE == COL_FMO && !std::is_same<T, double>::value);
+};
+
 template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE>
 __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     using C = cx_t<T>;
@@ -309,7 +343,15 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         bt = ((long long)blockIdx.y * (N / L) + blockIdx.x) * L + l;
     }
     constexpr bool ok = true;
+    using O = ColOpt<T, MODE>;
     const C *tw = reinterpret_cast<const C *>(a.tw);
+    if constexpr (O::TWS) {
+        // the roots table in shared memory after the exchange buffer (first
+        // read after the barrier that opens the second stage)
+        C *tws = buf + (size_t)n * (L + 1);
+        for (int e = threadIdx.x; e < n; e += L * TPL) tws[e] = ldg_c(tw + e);
+        tw = tws;
+    }
     // thread-relative bases: position p = t + c lives at base_t + c*POS
     const C *in_t = reinterpret_cast<const C *>(a.in) + bt * G::IN_BATCH + line + (long long)t * G::IN_POS;
     C *out_t = reinterpret_cast<C *>(a.out) + bt * G::OUT_BATCH + line + (long long)t * G::OUT_POS;
@@ -323,11 +365,27 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         StaticFor<0, HZ0 ? R1 / 2 : R1>::run([&](auto rc) {
             constexpr int r = decltype(rc)::value;
             constexpr long long c = k * TPL + r * (n / R1);
-            v[k * R1 + r] = ok ? in_t[c * G::IN_POS] : C{T(0), T(0)};
+            v[k * R1 + r] = ok ? ldcg_c(in_t + c * G::IN_POS) : C{T(0), T(0)};
         });
     });
-    Stg<T, D0, n, V, L>::template compute<R1, 1, HZ0, false>(v, t, tw);
-    run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV>(v, buf, t, l, tw, false);
+    if constexpr (O::PF) {
+        // prefetch this thread's spectrum values into L1: their latency then
+        // overlaps the forward transform instead of stalling the multiply
+        const int fy0 = (int)bt <= N ? (int)bt : n - (int)bt;
+        const T *Sy0 = reinterpret_cast<const T *>(a.S) + (long long)fy0 * G::S_BATCH + line;
+        StaticFor<0, V / RL>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            StaticFor<0, RL>::run([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr int c = k * TPL + r * (n / RL);
+                const int p = t + c;
+                const int fz = p <= N ? p : n - p;
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(Sy0 + (long long)fz * G::S_POS));
+            });
+        });
+    }
+    Stg<T, D0, n, V, L, O::TWS>::template compute<R1, 1, HZ0, false>(v, t, tw);
+    run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV, O::TWS>(v, buf, t, l, tw, false);
 
     if constexpr (G::ZL) {
         // multiply by the real, even spectrum at the folded frequency
@@ -372,13 +430,13 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         });
         // inverse, radix schedule reversed: its stage 0 is the forward's last
         // radix on the same butterflies, already in registers
-        using SI = Stg<T, +1, n, V, L>;
+        using SI = Stg<T, +1, n, V, L, O::TWS>;
         if constexpr (R3 > 1) {
             SI::template compute<R3, 1, false, false>(v, t, tw);
-            run_rest<T, +1, n, V, L, R3, R2, R1, true>(v, buf, t, l, tw, true);
+            run_rest<T, +1, n, V, L, R3, R2, R1, true, O::TWS>(v, buf, t, l, tw, true);
         } else {
             SI::template compute<R2, 1, false, false>(v, t, tw);
-            run_rest<T, +1, n, V, L, R2, R1, 1, true>(v, buf, t, l, tw, true);
+            run_rest<T, +1, n, V, L, R2, R1, 1, true, O::TWS>(v, buf, t, l, tw, true);
         }
         constexpr int RF = R1;  // last radix of the reversed schedule
         StaticFor<0, V / RF>::run([&](auto kc) {
@@ -598,7 +656,7 @@ template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a
         return cudaErrorInvalidValue;
     } else {
         auto kern = k_fast_col<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE>;
-        const size_t sm = smem_for<T, n>(n);
+        const size_t sm = smem_for<T, n>(n) + (ColOpt<T, MODE>::TWS ? sizeof(cx_t<T>) * n : 0);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         // N/L full tiles per batch row, plus nbatch/N block rows of Nyquist tiles

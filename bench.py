@@ -313,12 +313,13 @@ def pass_bytes3(n, c, r):
 def noncubic_leg(fsp, n, L, K, W, world, hbm, hbm_kind):
     """The 1 x 1 x 2 box of the paper's weak-scaling runs (Sec. 3.2) at
     n = (n_x, n_y, n_z), VG-DCT (the memory-reduced form: the (4n)^3 grid of
-    plain VG would not fit), FP32-mixed and FP64, generic engine; per-pass
+    plain VG would not fit at 512^2 x 1024), FP32-mixed and FP64; per-pass
     events give the dominant pass's roofline."""
     import torch
     out = {}
     for dtype, c, r in (("f32", 8, 4), ("f64", 16, 8)):
         plan = fsp.Plan(n, L, "vg_dct", dtype)
+        fast = plan.fast_path
         tdt = torch.float32 if dtype == "f32" else torch.float64
         srcs = [torch.from_numpy(I.gaussian_mixture3(n, L, seed=2405 + i).astype(np.float32)).to(tdt).cuda()
                 for i in range(2)]
@@ -350,7 +351,9 @@ def noncubic_leg(fsp, n, L, K, W, world, hbm, hbm_kind):
         t = tmax / k
         out[dtype] = {"value": round(value, 2), "unit": "solves/s", "steps": k, "ms_per_step": round(t, 4),
                       "hbm_gbs_solve": round(sum(pb) / (t * 1e-3) / 1e9, 1),
-                      "roofline": {"bound": "hbm", "kernel": PASS_NAMES[kk].split(" (")[0] + " (generic engine)",
+                      "roofline": {"bound": "hbm",
+                                   "kernel": PASS_NAMES[kk].split(" (")[0]
+                                   + (" (specialised kernels, runtime strides)" if fast else " (generic engine)"),
                                    "achieved": round(pb[kk] / dur / 1e9, 1), "peak": hbm, "unit": "GB/s",
                                    "frac": round(pb[kk] / dur / 1e9 / hbm, 4),
                                    "peak_kind": hbm_kind + " copy bandwidth",

@@ -654,11 +654,49 @@ cudaError_t enqueue_solve_aniso(const fsp_plan *p, const void *rho, void *phi, v
     return mark(5);
 }
 
+// The same on the specialised kernels (every n_a a power of two in [32, 512]):
+// the rows depend on n_x only; the column passes take runtime geometry.
+template <typename T>
+cudaError_t enqueue_solve_aniso_fast(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
+    const int nx = p->n3[0], ny = p->n3[1], nz = p->n3[2];
+    const long long P = p->P;
+    cudaError_t e;
+    auto mark = [&](int i) { return p->timing ? cudaEventRecord(p->ev[i], s) : cudaSuccess; };
+    fast::RowArgs r{};
+    r.x = rho, r.c = W1, r.x_row = nx, r.c_row = P, r.nrows = ny * nz, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+    if ((e = mark(0)) != cudaSuccess) return e;
+    if ((e = fast::p1<T>(nx, r, s)) != cudaSuccess) return e;
+    if ((e = mark(1)) != cudaSuccess) return e;
+    fast::ColArgs a{};
+    a.nlines = nx + 1;
+    a.tw = p->tw_y, a.in = W1, a.out = W2;
+    a.in_pos = P, a.in_batch = (long long)ny * P, a.out_pos = P, a.out_batch = 2LL * ny * P;
+    if ((e = fast::col_rg<T>(fast::COL_FWD, 2 * ny, a, nz, s)) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
+    a.tw = p->tw_z, a.in = a.out = W2;
+    a.in_pos = a.out_pos = 2LL * ny * P, a.in_batch = a.out_batch = P;
+    a.S = p->S, a.s_pos = (long long)(ny + 1) * P, a.s_batch = P, a.half = nz, a.half_b = ny;
+    if ((e = fast::col_rg<T>(fast::COL_FMI, 2 * nz, a, 2 * ny, s)) != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
+    a.tw = p->tw_y, a.in = W2, a.out = W1;
+    a.in_pos = P, a.in_batch = 2LL * ny * P, a.out_pos = P, a.out_batch = (long long)ny * P;
+    if ((e = fast::col_rg<T>(fast::COL_INV, 2 * ny, a, nz, s)) != cudaSuccess) return e;
+    if ((e = mark(4)) != cudaSuccess) return e;
+    r.x = phi;
+    if ((e = fast::p5<T>(nx, r, s)) != cudaSuccess) return e;
+    return mark(5);
+}
+
 // One solve of plan p with the given workspace (W1: N*N*P, W2: 2*N*N*P complex).
 cudaError_t enqueue_solve_ws(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
-    if (p->aniso)
+    if (p->aniso) {
+        if (p->fast)
+            return p->dtype == FSP_F64      ? enqueue_solve_aniso_fast<double>(p, rho, phi, W1, W2, s)
+                   : p->dtype == FSP_F64_DF ? enqueue_solve_aniso_fast<df>(p, rho, phi, W1, W2, s)
+                                            : enqueue_solve_aniso_fast<float>(p, rho, phi, W1, W2, s);
         return p->dtype == FSP_F64 ? enqueue_solve_aniso<double>(p, rho, phi, W1, W2, s)
                                    : enqueue_solve_aniso<float>(p, rho, phi, W1, W2, s);
+    }
     if (p->dtype == FSP_F64_DF) return enqueue_solve_fast<df>(p, rho, phi, W1, W2, s);
     if (p->fast)
         return p->dtype == FSP_F64 ? enqueue_solve_fast<double>(p, rho, phi, W1, W2, s)
@@ -799,7 +837,19 @@ fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double 
     }
     if (nx == ny && ny == nz && hx == hy && hy == hz)  // a cube: the cubic plan and its kernels
         return plan_create_impl(out, nx, nx * hx, hx, algo, dtype, stream, true);
-    if (dtype == FSP_F64_DF) return FSP_EUNSUPPORTED;  // double-float: specialised cubic kernels only
+    // the specialised kernels when every n_a has them (and FSP_GENERIC_ONLY is not 1)
+    bool fast_ok;
+    {
+        const char *g = std::getenv("FSP_GENERIC_ONLY");
+        const bool generic_only = g && g[0] == '1';
+        fast_ok = true;
+        for (int a = 0; a < 3; ++a)
+            fast_ok = fast_ok && (dtype == FSP_F64      ? fast::has<double>(nn[a])
+                                  : dtype == FSP_F64_DF ? fast::has<df>(nn[a])
+                                                        : fast::has<float>(nn[a]));
+        if (dtype != FSP_F64_DF) fast_ok = fast_ok && !generic_only;
+    }
+    if (dtype == FSP_F64_DF && !fast_ok) return FSP_EUNSUPPORTED;  // double-float: specialised kernels only
     if (algo != FSP_HE) {
         // the (4 n_a h_a) periodisation of the truncated kernel must not reach
         // the box: 3 min_a L_a >= L_t = alpha |(L_x, L_y, L_z)|
@@ -811,6 +861,7 @@ fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double 
     const auto t0 = std::chrono::steady_clock::now();
     fsp_plan *p = new fsp_plan();
     p->aniso = true;
+    p->fast = fast_ok;
     for (int a = 0; a < 3; ++a) p->n3[a] = nn[a], p->h3[a] = hh[a];
     p->N = nx, p->L = nx * hx, p->h = hx, p->algo = algo, p->dtype = dtype;
     p->rsize = dtype == FSP_F32_MIXED ? 4 : 8;
@@ -851,6 +902,11 @@ fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double 
         if (e == cudaSuccess) e = launch_roots<double>(p->tw_2n, 2 * nx, s);
         if (e == cudaSuccess) e = launch_roots<double>(p->tw_y, 2 * ny, s);
         if (e == cudaSuccess) e = launch_roots<double>(p->tw_z, 2 * nz, s);
+    } else if (dtype == FSP_F64_DF) {
+        e = launch_roots<df>(p->tw_n, nx, s);
+        if (e == cudaSuccess) e = launch_roots<df>(p->tw_2n, 2 * nx, s);
+        if (e == cudaSuccess) e = launch_roots<df>(p->tw_y, 2 * ny, s);
+        if (e == cudaSuccess) e = launch_roots<df>(p->tw_z, 2 * nz, s);
     } else {
         e = launch_roots<float>(p->tw_n, nx, s);
         if (e == cudaSuccess) e = launch_roots<float>(p->tw_2n, 2 * nx, s);
@@ -866,8 +922,9 @@ fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double 
         if ((st = enqueue_kernel_T3(nn, hh, algo, (double *)Td.p, s, tmp)) != FSP_OK) return fail(st);
         if ((st = enqueue_trig_spectrum3(nn, -1, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
         const double scale = hx * hy * hz / ((2.0 * nx) * (2.0 * ny) * (2.0 * nz));
-        e = dtype == FSP_F64 ? launch_store_S3<double>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s)
-                             : launch_store_S3<float>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s);
+        e = dtype == FSP_F64      ? launch_store_S3<double>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s)
+            : dtype == FSP_F64_DF ? launch_store_S3<df>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s)
+                                  : launch_store_S3<float>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s);
         if (e != cudaSuccess) return fail(FSP_ECUDA);
         if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FSP_ECUDA);
     }
@@ -1091,8 +1148,9 @@ fsp_status fsp_plan_spectrum(const fsp_plan *plan, double *s_host) {
         DevBuf d;
         fsp_status st = alloc_or_nomem(d, sizeof(double) * tot);
         if (st != FSP_OK) return st;
-        cudaError_t e = plan->dtype == FSP_F64 ? launch_load_S3<double>(plan->S, (double *)d.p, kx, rows, plan->P, 0)
-                                               : launch_load_S3<float>(plan->S, (double *)d.p, kx, rows, plan->P, 0);
+        cudaError_t e = plan->dtype == FSP_F64      ? launch_load_S3<double>(plan->S, (double *)d.p, kx, rows, plan->P, 0)
+                        : plan->dtype == FSP_F64_DF ? launch_load_S3<df>(plan->S, (double *)d.p, kx, rows, plan->P, 0)
+                                                    : launch_load_S3<float>(plan->S, (double *)d.p, kx, rows, plan->P, 0);
         if (e != cudaSuccess) return FSP_ECUDA;
         return cuda_status(cudaMemcpy(s_host, d.p, sizeof(double) * tot, cudaMemcpyDeviceToHost));
     }

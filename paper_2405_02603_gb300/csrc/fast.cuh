@@ -318,12 +318,19 @@ template <typename T, int MODE> struct ColOpt {
     static constexpr bool TWS = (DF && MODE != COL_INV) || (MODE == COL_FMO && !std::is_same<T, double>::value);
 };
 
-template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE>
+// RG (a non-cubic box): the strides, the number of lines (k_x <= n_x) and the
+// fold of the batch index (k_y <= n_y) come from the arguments instead of
+// ColGeo; the cube keeps its compile-time geometry.
+template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG = false>
 __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     using C = cx_t<T>;
     using G = ColGeo<n, MODE>;
     constexpr int TPL = n / V, N = G::N;
     constexpr int RL = LastR<R1, R2, R3>::value;
+    const long long IN_POS = RG ? a.in_pos : G::IN_POS, IN_BATCH = RG ? a.in_batch : G::IN_BATCH;
+    const long long OUT_POS = RG ? a.out_pos : G::OUT_POS, OUT_BATCH = RG ? a.out_batch : G::OUT_BATCH;
+    const long long S_POS = RG ? a.s_pos : G::S_POS, S_BATCH = RG ? a.s_batch : G::S_BATCH;
+    const int HB = RG ? a.half_b : N;  // fold of the batch index in P3
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     const int l = threadIdx.x % L, t = threadIdx.x / L;
@@ -331,16 +338,29 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     // The Nyquist column k_x = N runs in the first X = NB/N block rows, whose
     // tile's L lines are L consecutive batch indices of that one column (their
     // loads are strided, so they go first rather than form the last wave).
-    constexpr int NB = G::ZL ? 2 * N : N;  // batch rows (k_y or z)
-    constexpr int X = NB / N;
+    // RG: N -> n_x = nlines - 1 and X = a.xrows rows of gridDim.x tiles.
     int line;
     long long bt;
-    if ((int)blockIdx.y >= X) {
-        line = blockIdx.x * L + l;
-        bt = blockIdx.y - X;
+    if constexpr (!RG) {
+        constexpr int NB = G::ZL ? 2 * N : N;  // batch rows (k_y or z)
+        constexpr int X = NB / N;
+        if ((int)blockIdx.y >= X) {
+            line = blockIdx.x * L + l;
+            bt = blockIdx.y - X;
+        } else {
+            line = N;
+            bt = ((long long)blockIdx.y * (N / L) + blockIdx.x) * L + l;
+        }
     } else {
-        line = N;
-        bt = ((long long)blockIdx.y * (N / L) + blockIdx.x) * L + l;
+        if ((int)blockIdx.y >= a.xrows) {
+            line = blockIdx.x * L + l;
+            bt = blockIdx.y - a.xrows;
+        } else {
+            const long long q = (long long)blockIdx.y * gridDim.x + blockIdx.x;  // Nyquist tile
+            if (q * L >= a.nbatch) return;  // the whole block: before any barrier
+            line = a.nlines - 1;
+            bt = q * L + l;
+        }
     }
     constexpr bool ok = true;
     using O = ColOpt<T, MODE>;
@@ -353,8 +373,8 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         tw = tws;
     }
     // thread-relative bases: position p = t + c lives at base_t + c*POS
-    const C *in_t = reinterpret_cast<const C *>(a.in) + bt * G::IN_BATCH + line + (long long)t * G::IN_POS;
-    C *out_t = reinterpret_cast<C *>(a.out) + bt * G::OUT_BATCH + line + (long long)t * G::OUT_POS;
+    const C *in_t = reinterpret_cast<const C *>(a.in) + bt * IN_BATCH + line + (long long)t * IN_POS;
+    C *out_t = reinterpret_cast<C *>(a.out) + bt * OUT_BATCH + line + (long long)t * OUT_POS;
     C v[V];
 
     // stage 0 inputs straight from global memory
@@ -365,14 +385,14 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         StaticFor<0, HZ0 ? R1 / 2 : R1>::run([&](auto rc) {
             constexpr int r = decltype(rc)::value;
             constexpr long long c = k * TPL + r * (n / R1);
-            v[k * R1 + r] = ok ? ldcg_c(in_t + c * G::IN_POS) : C{T(0), T(0)};
+            v[k * R1 + r] = ok ? ldcg_c(in_t + c * IN_POS) : C{T(0), T(0)};
         });
     });
     if constexpr (O::PF) {
         // prefetch this thread's spectrum values into L1: their latency then
         // overlaps the forward transform instead of stalling the multiply
-        const int fy0 = (int)bt <= N ? (int)bt : n - (int)bt;
-        const T *Sy0 = reinterpret_cast<const T *>(a.S) + (long long)fy0 * G::S_BATCH + line;
+        const int fy0 = (int)bt <= HB ? (int)bt : 2 * HB - (int)bt;
+        const T *Sy0 = reinterpret_cast<const T *>(a.S) + (long long)fy0 * S_BATCH + line;
         StaticFor<0, V / RL>::run([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             StaticFor<0, RL>::run([&](auto rc) {
@@ -380,7 +400,7 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
                 constexpr int c = k * TPL + r * (n / RL);
                 const int p = t + c;
                 const int fz = p <= N ? p : n - p;
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(Sy0 + (long long)fz * G::S_POS));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(Sy0 + (long long)fz * S_POS));
             });
         });
     }
@@ -390,13 +410,13 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
     if constexpr (G::ZL) {
         // multiply by the real, even spectrum at the folded frequency
         // min(p, n - p); for most registers the branch is known at compile time
-        const int fy = (int)bt <= N ? (int)bt : n - (int)bt;
-        const T *Sy = reinterpret_cast<const T *>(a.S) + (long long)fy * G::S_BATCH + line;
-        const T *S_up = Sy + (long long)t * G::S_POS, *S_dn = Sy - (long long)t * G::S_POS;
+        const int fy = (int)bt <= HB ? (int)bt : 2 * HB - (int)bt;
+        const T *Sy = reinterpret_cast<const T *>(a.S) + (long long)fy * S_BATCH + line;
+        const T *S_up = Sy + (long long)t * S_POS, *S_dn = Sy - (long long)t * S_POS;
         // COL_FMO (a field component): the spectrum is odd in z (a.odd = 1),
         // k_y (2) or k_x (3); the multiplier is -i S[fold], negated past the
         // fold in z (per register) or k_y (per thread); k_x <= N never flips
-        const T sy = MODE == COL_FMO && a.odd == 2 && (int)bt > N ? T(-1) : T(1);
+        const T sy = MODE == COL_FMO && a.odd == 2 && (int)bt > HB ? T(-1) : T(1);
         const bool oz = MODE == COL_FMO && a.odd == 1;
         StaticFor<0, V / RL>::run([&](auto kc) {
             constexpr int k = decltype(kc)::value;
@@ -406,15 +426,15 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
                 T s;
                 bool upper;  // z = t + c > N
                 if constexpr (c + TPL - 1 <= N) {
-                    s = ok ? S_up[(long long)c * G::S_POS] : T(0);
+                    s = ok ? S_up[(long long)c * S_POS] : T(0);
                     upper = false;
                 } else if constexpr (c > N) {
-                    s = ok ? S_dn[(long long)(n - c) * G::S_POS] : T(0);
+                    s = ok ? S_dn[(long long)(n - c) * S_POS] : T(0);
                     upper = true;
                 } else {
                     const int p = t + c;
                     const int fz = p <= N ? p : n - p;
-                    s = ok ? Sy[(long long)fz * G::S_POS] : T(0);
+                    s = ok ? Sy[(long long)fz * S_POS] : T(0);
                     upper = p > N;
                 }
                 if constexpr (MODE == COL_FMI) {
@@ -444,7 +464,7 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
             StaticFor<0, RF / 2>::run([&](auto rc) {
                 constexpr int r = decltype(rc)::value;
                 constexpr long long c = k * TPL + r * (n / RF);
-                if (ok) out_t[c * G::OUT_POS] = v[k * RF + r];
+                if (ok) out_t[c * OUT_POS] = v[k * RF + r];
             });
         });
     } else {
@@ -454,7 +474,7 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
             StaticFor<0, HO ? RL / 2 : RL>::run([&](auto rc) {
                 constexpr int r = decltype(rc)::value;
                 constexpr long long c = k * TPL + r * (n / RL);
-                if (ok) out_t[c * G::OUT_POS] = v[k * RL + r];
+                if (ok) out_t[c * OUT_POS] = v[k * RL + r];
             });
         });
     }
@@ -624,7 +644,7 @@ FSP_CFG(float, 64, 8, 16, 8, 8, 1)
 FSP_CFG(float, 128, 16, 16, 8, 16, 1)
 FSP_CFG(float, 256, 16, 16, 16, 16, 1)
 FSP_CFG(float, 512, 32, 16, 16, 32, 1)
-FSP_CFG(float, 1024, 32, 8, 32, 32, 1)
+FSP_CFG(float, 1024, 16, 16, 16, 16, 4)
 FSP_CFG(double, 32, 8, 16, 4, 8, 1)
 FSP_CFG(double, 64, 8, 16, 8, 8, 1)
 FSP_CFG(double, 128, 16, 8, 8, 16, 1)
@@ -639,6 +659,15 @@ FSP_CFG(df, 512, 8, 8, 8, 8, 8)
 FSP_CFG(df, 1024, 16, 8, 16, 8, 8)
 #undef FSP_CFG
 
+// A column pass may override its length's shape: at n = 1024 the FP32
+// inverse-only pass (P4) is faster with V = 32, L = 8, 32*32 (0.66 vs 0.80 ms
+// at N = 512), the passes with a forward transform with V = 16, L = 16, 16*16*4.
+template <typename T, int n, int MODE> struct ColCfg : Cfg<T, n> {};
+template <> struct ColCfg<float, 1024, COL_INV> {
+    static constexpr bool Ok = true;
+    static constexpr int V = 32, L = 8, R1 = 32, R2 = 32, R3 = 1;
+};
+
 template <typename T, int n> constexpr size_t smem_for(int positions) {
     return (size_t)positions * (Cfg<T, n>::L + 1) * sizeof(cx_t<T>);
 }
@@ -651,12 +680,12 @@ namespace fsp {
 namespace fast {
 
 template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a, int nbatch, cudaStream_t s) {
-    using K = Cfg<T, n>;
+    using K = ColCfg<T, n, MODE>;
     if constexpr (!K::Ok) {
         return cudaErrorInvalidValue;
     } else {
         auto kern = k_fast_col<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE>;
-        const size_t sm = smem_for<T, n>(n) + (ColOpt<T, MODE>::TWS ? sizeof(cx_t<T>) * n : 0);
+        const size_t sm = sizeof(cx_t<T>) * n * (K::L + 1) + (ColOpt<T, MODE>::TWS ? sizeof(cx_t<T>) * n : 0);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         // N/L full tiles per batch row, plus nbatch/N block rows of Nyquist tiles
@@ -667,6 +696,39 @@ template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a
         kern<<<grid, K::L * (n / K::V), sm, s>>>(a);
         return cudaGetLastError();
     }
+}
+
+// Non-cubic box: lines k_x <= n_x = nlines - 1 (a multiple of L), nbatch a
+// multiple of L; ceil(nbatch / n_x) leading block rows hold the Nyquist tiles.
+template <typename T, int n, int MODE> cudaError_t launch_col_rg_n(const ColArgs &a, int nbatch, cudaStream_t s) {
+    using K = ColCfg<T, n, MODE>;
+    if constexpr (!K::Ok) {
+        return cudaErrorInvalidValue;
+    } else {
+        auto kern = k_fast_col<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE, true>;
+        const int nx = a.nlines - 1;
+        if (nx <= 0 || nx % K::L != 0 || nbatch % K::L != 0) return cudaErrorInvalidValue;
+        ColArgs b = a;
+        b.nbatch = nbatch;
+        b.xrows = (nbatch / K::L + nx / K::L - 1) / (nx / K::L);
+        const size_t sm = sizeof(cx_t<T>) * n * (K::L + 1) + (ColOpt<T, MODE>::TWS ? sizeof(cx_t<T>) * n : 0);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(nx / K::L), (unsigned)(nbatch + b.xrows));
+        kern<<<grid, K::L * (n / K::V), sm, s>>>(b);
+        return cudaGetLastError();
+    }
+}
+
+template <typename T, int MODE> cudaError_t launch_col_rg(int n, const ColArgs &a, int nbatch, cudaStream_t s) {
+    switch (n) {
+    case 64: return launch_col_rg_n<T, 64, MODE>(a, nbatch, s);
+    case 128: return launch_col_rg_n<T, 128, MODE>(a, nbatch, s);
+    case 256: return launch_col_rg_n<T, 256, MODE>(a, nbatch, s);
+    case 512: return launch_col_rg_n<T, 512, MODE>(a, nbatch, s);
+    case 1024: return launch_col_rg_n<T, 1024, MODE>(a, nbatch, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename T, int N, bool R2C> cudaError_t launch_row_n(const RowArgs &a, cudaStream_t s) {
@@ -718,6 +780,18 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
     }                                                                                                          \
     template <> cudaError_t p4<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
         return launch_col<T, COL_INV>(2 * N, a, nb, s);                                                        \
+    }
+
+// the column passes of non-cubic boxes (runtime geometry), in translation
+// units of their own
+#define FSP_FAST_RG_INSTANTIATE(T)                                                                             \
+    template <> cudaError_t col_rg<T>(int mode, int n, const ColArgs &a, int nb, cudaStream_t s) {              \
+        switch (mode) {                                                                                        \
+        case COL_FWD: return launch_col_rg<T, COL_FWD>(n, a, nb, s);                                           \
+        case COL_INV: return launch_col_rg<T, COL_INV>(n, a, nb, s);                                           \
+        case COL_FMI: return launch_col_rg<T, COL_FMI>(n, a, nb, s);                                           \
+        }                                                                                                      \
+        return cudaErrorInvalidValue;                                                                          \
     }
 
 // the field's P3 (odd spectrum), in translation units of its own

@@ -20,6 +20,10 @@ struct ColArgs {
     // position), k_y (the batch) or k_x (the line): the multiplier is
     // -i S[fold], negated where z or k_y > N.  Ignored by p3.
     int odd;
+    // col_rg (a non-cubic box): the fold of the batch index k_y in P3 (n_y);
+    // nbatch and xrows are set by the launcher
+    int half_b;
+    int nbatch, xrows;
 };
 
 // Row pass: rows of N reals (x, stride x_row) <-> rows of N+1 complex (c,
@@ -43,6 +47,9 @@ template <typename T> cudaError_t p2(int N, const ColArgs &a, int nbatch, cudaSt
 template <typename T> cudaError_t p3(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 template <typename T> cudaError_t p4(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 template <typename T> cudaError_t p5(int N, const RowArgs &a, cudaStream_t s);
+// A column pass (mode COL_FWD, COL_INV or COL_FMI) of length n on a non-cubic
+// box: strides from `a`, lines k_x <= a.nlines - 1, P3's k_y fold at a.half_b
+template <typename T> cudaError_t col_rg(int mode, int n, const ColArgs &a, int nbatch, cudaStream_t s);
 // P3 of a field component: z-FFT * (-i S_a, odd in the axis a.odd) * z-IFFT
 template <typename T> cudaError_t p3_odd(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 

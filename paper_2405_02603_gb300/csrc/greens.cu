@@ -255,5 +255,7 @@ template cudaError_t launch_store_S3<float>(const double *, void *, int, long lo
 template cudaError_t launch_store_S3<double>(const double *, void *, int, long long, int, double, cudaStream_t);
 template cudaError_t launch_load_S3<float>(const void *, double *, int, long long, int, cudaStream_t);
 template cudaError_t launch_load_S3<double>(const void *, double *, int, long long, int, cudaStream_t);
+template cudaError_t launch_store_S3<df>(const double *, void *, int, long long, int, double, cudaStream_t);
+template cudaError_t launch_load_S3<df>(const void *, double *, int, long long, int, cudaStream_t);
 
 }  // namespace fsp

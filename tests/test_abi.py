@@ -60,7 +60,8 @@ def test_aniso_plan_validation_needs_no_device(L):
     # 2 n_a not smooth, n_a too large, 4 n_a not smooth for VG
     assert c(ctypes.byref(p), 8, 7, 8, 0.1, 0.1, 0.1, 0, 0, None) == 2
     assert c(ctypes.byref(p), 8, 8, 2048, 0.1, 0.1, 0.1, 0, 0, None) == 2
-    # the Vico-Greengard window beyond 3 min L_a (1 x 1 x 2.5 box), double-float on a non-cube
+    # the Vico-Greengard window beyond 3 min L_a (1 x 1 x 2.5 box); double-float on a non-cube
+    # without the specialised kernels (n_a = 16)
     assert c(ctypes.byref(p), 16, 16, 40, 1.0 / 16, 1.0 / 16, 1.0 / 16, 1, 0, None) == 2
     assert c(ctypes.byref(p), 16, 16, 40, 1.0 / 16, 1.0 / 16, 1.0 / 16, 2, 0, None) == 2
     assert c(ctypes.byref(p), 16, 16, 32, 1.0 / 16, 1.0 / 16, 1.0 / 16, 0, 2, None) == 2

@@ -3,9 +3,11 @@
 Whole fields against the oracle's full doubled-grid FFT on boxes with three
 different sizes and spacings (ragged tiles in every axis, an axis of 2 cells,
 the 1 x 1 x 2 shape of the paper's weak-scaling runs), every method in both
-precisions; the cubic case returns the cubic plan; the spectrum against the
-oracle's; a 256 x 256 x 512 Hockney-Eastwood solve at sampled points against
-the oracle's direct sum."""
+precisions, on the generic engine; power-of-two boxes on the specialised
+kernels with runtime geometry in all three dtypes (and against the generic
+engine); the cubic case returns the cubic plan; the spectrum against the
+oracle's; a 256 x 256 x 512 solve at sampled points against the oracle's
+direct sum."""
 import numpy as np
 import pytest
 
@@ -39,6 +41,38 @@ def test_aniso_whole_field(fsp, orc, n, L, algo, dtype):
     print("aniso %s %s %s E_max %.2e" % (n, algo, dtype, err))
     assert err <= TOL[dtype]
     p.close()
+
+
+FAST_BOXES = [((32, 64, 128), (1.0, 1.0, 2.0)), ((64, 32, 32), (1.2, 1.0, 0.8)), ((128, 32, 64), (1.0, 0.6, 0.8))]
+TOL3 = {"f64": 1e-12, "f32": 2e-6, "f64df": 1e-12}
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f64df"])
+@pytest.mark.parametrize("algo", ["he", "vg_dct"])
+@pytest.mark.parametrize("n,L", FAST_BOXES)
+def test_aniso_fast_path(fsp, orc, n, L, algo, dtype):
+    h = _h(n, L)
+    rho = I.gaussian_mixture3(n, L, seed=11 + n[2]).astype(np.float32).astype(np.float64)
+    p = fsp.Plan(n, L, algo, dtype)
+    assert p.fast_path
+    phi = p.solve(to_dev(rho, dtype)).cpu().numpy()
+    ref = orc.solve_fft3(orc.kernel_T3(algo, n, h), rho, h)
+    err = e_max(phi, ref)
+    print("aniso fast %s %s %s E_max %.2e" % (n, algo, dtype, err))
+    assert err <= TOL3[dtype]
+    p.close()
+
+
+def test_aniso_fast_equals_generic(fsp, monkeypatch):
+    n, L = (64, 32, 128), (1.0, 1.0, 1.5)
+    rho = to_dev(I.gaussian_mixture3(n, L, seed=5), "f64")
+    a = fsp.Plan(n, L, "vg", "f64")
+    monkeypatch.setenv("FSP_GENERIC_ONLY", "1")
+    b = fsp.Plan(n, L, "vg", "f64")
+    assert a.fast_path and not b.fast_path
+    assert e_max(a.solve(rho).cpu().numpy(), b.solve(rho).cpu().numpy()) < 1e-14
+    a.close()
+    b.close()
 
 
 @pytest.mark.parametrize("algo", ["he", "vg_dct"])
@@ -88,14 +122,16 @@ def test_aniso_plan_rejects_field_and_batch(fsp):
     p.close()
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f64df"])
 def test_aniso_256x256x512_sampled(fsp, orc, dtype):
-    """The 1 x 1 x 2 shape of the weak-scaling runs at 256^2 x 512, HE, at
-    sampled points against the oracle's direct O(N^3) sum per point."""
+    """The 1 x 1 x 2 shape of the weak-scaling runs at 256^2 x 512 (the
+    specialised kernels), HE, at sampled points against the oracle's direct
+    O(N^3) sum per point."""
     n, L = (256, 256, 512), (1.0, 1.0, 2.0)
     h = _h(n, L)
     rho = I.gaussian_mixture3(n, L).astype(np.float32).astype(np.float64)
     p = fsp.Plan(n, L, "he", dtype)
+    assert p.fast_path
     phi = p.solve(to_dev(rho, dtype)).cpu().numpy().ravel()
     rng = np.random.default_rng(2565)
     tot = n[0] * n[1] * n[2]
@@ -103,5 +139,5 @@ def test_aniso_256x256x512_sampled(fsp, orc, dtype):
     ref = orc.solve_direct3(orc.kernel_T3("he", n, h), rho, h, pts)
     err = float(np.max(np.abs(phi[pts] - ref)) / np.max(np.abs(ref)))
     print("256x256x512 he %s sampled E_max %.2e" % (dtype, err))
-    assert err <= TOL[dtype]
+    assert err <= TOL3[dtype]
     p.close()

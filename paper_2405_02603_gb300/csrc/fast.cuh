@@ -659,13 +659,19 @@ FSP_CFG(df, 512, 8, 8, 8, 8, 8)
 FSP_CFG(df, 1024, 16, 8, 16, 8, 8)
 #undef FSP_CFG
 
-// A column pass may override its length's shape: at n = 1024 the FP32
-// inverse-only pass (P4) is faster with V = 32, L = 8, 32*32 (0.66 vs 0.80 ms
-// at N = 512), the passes with a forward transform with V = 16, L = 16, 16*16*4.
+// A column pass may override its length's shape (each measured on the GB300):
+// at n = 1024 the FP32 inverse-only pass (P4) is faster with V = 32, L = 8,
+// 32*32 (0.66 vs 0.80 ms at N = 512), the passes with a forward transform with
+// V = 16, L = 16, 16*16*4; at n = 512 P4 is faster with V = 16, L = 16,
+// 16*16*2 (0.078 vs 0.092 ms at N = 256), P2 and P3 with V = 32, L = 16, 16*32.
 template <typename T, int n, int MODE> struct ColCfg : Cfg<T, n> {};
 template <> struct ColCfg<float, 1024, COL_INV> {
     static constexpr bool Ok = true;
     static constexpr int V = 32, L = 8, R1 = 32, R2 = 32, R3 = 1;
+};
+template <> struct ColCfg<float, 512, COL_INV> {
+    static constexpr bool Ok = true;
+    static constexpr int V = 16, L = 16, R1 = 16, R2 = 16, R3 = 2;
 };
 
 template <typename T, int n> constexpr size_t smem_for(int positions) {

@@ -24,7 +24,9 @@ error metrics.  Every function names the passage of the paper it follows:
   DST-I/DCT-I mix an odd kernel's octant needs.
 - ``kernel_T3``, ``solve_fft3``, ``spectrum3``, ``solve_direct3``, ``solve3``:
   the methods on a non-cubic box of n_x x n_y x n_z cells with spacings
-  h_x, h_y, h_z (the shapes of the paper's weak-scaling runs, Sec. 3.2).
+  h_x, h_y, h_z (the shapes of the paper's weak-scaling runs, Sec. 3.2), and
+  ``field_kernel3``, ``solve_field_fft3``, ``solve_field_direct3``,
+  ``solve_field3`` for the field on them.
 - ``field_kernel``, ``solve_field_fft``, ``solve_field_direct``,
   ``field_spectrum``, ``solve_field``: the field E = -grad phi (Appendix B,
   Eq. efield) as the convolution of rho with F = -grad G of each method.
@@ -75,6 +77,9 @@ def _load():
         lib.orc_solve_fft3.argtypes = [ip, dp, dp, dp, dp]
         lib.orc_spectrum3.argtypes = [ip, dp, dp, dp]
         lib.orc_solve_direct3.argtypes = [ip, dp, dp, dp, lp, ctypes.c_longlong, dp]
+        lib.orc_field_kernel3.argtypes = [i, i, ip, dp, d, dp]
+        lib.orc_solve_field_fft3.argtypes = [ip, dp, i, dp, dp, dp]
+        lib.orc_solve_field_direct3.argtypes = [ip, dp, i, dp, dp, lp, ctypes.c_longlong, dp]
         _lib = lib
     return _lib
 
@@ -350,11 +355,57 @@ def solve3(algo, rho, h, alpha=ALPHA):
     return solve_fft3(kernel_T3(algo, n, h, alpha), rho, h)
 
 
+def field_kernel3(algo, a, n, h, alpha=ALPHA):
+    """Field kernel F_a on a non-cubic box, shape (n_z+1, n_y+1, n_x+1)."""
+    algo = ALGOS.get(algo, algo)
+    nn, hh = _dims(n, h)
+    F = np.empty((n[2] + 1, n[1] + 1, n[0] + 1), dtype=np.float64)
+    _load().orc_field_kernel3(int(algo), int(a), nn, _p(hh), float(alpha), _p(F))
+    return F
+
+
+def solve_field_fft3(F, a, rho, h):
+    """E_a through the full doubled grid of a non-cubic box."""
+    F, rho = _f64(F), _f64(rho)
+    n = (rho.shape[2], rho.shape[1], rho.shape[0])
+    assert F.shape == (n[2] + 1, n[1] + 1, n[0] + 1)
+    nn, hh = _dims(n, h)
+    E = np.empty_like(rho)
+    _load().orc_solve_field_fft3(nn, _p(hh), int(a), _p(F), _p(rho), _p(E))
+    return E
+
+
+def solve_field_direct3(F, a, rho, h, points=None):
+    """E_a by its defining sum on a non-cubic box, at flat indices (or all)."""
+    F, rho = _f64(F), _f64(rho)
+    n = (rho.shape[2], rho.shape[1], rho.shape[0])
+    assert F.shape == (n[2] + 1, n[1] + 1, n[0] + 1)
+    nn, hh = _dims(n, h)
+    lib = _load()
+    if points is None:
+        out = np.empty_like(rho)
+        lib.orc_solve_field_direct3(nn, _p(hh), int(a), _p(F), _p(rho), None, 0, _p(out))
+        return out
+    pts = np.ascontiguousarray(points, dtype=np.int64).ravel()
+    assert pts.size == 0 or (pts.min() >= 0 and pts.max() < rho.size)
+    out = np.empty(pts.size, dtype=np.float64)
+    lib.orc_solve_field_direct3(nn, _p(hh), int(a), _p(F), _p(rho),
+                                pts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), pts.size, _p(out))
+    return out
+
+
+def solve_field3(algo, rho, h, alpha=ALPHA):
+    """(E_x, E_y, E_z) on a non-cubic box (rho indexed [z,y,x])."""
+    n = (rho.shape[2], rho.shape[1], rho.shape[0])
+    return tuple(solve_field_fft3(field_kernel3(algo, a, n, h, alpha), a, rho, h) for a in range(3))
+
+
 from . import analytic  # noqa: E402  (pure-numpy helpers, no C)
 
 __all__ = ["HE", "VG", "VG_DCT", "ALPHA", "dft1d", "fft1d", "fft3d", "dct1", "dct1_3d",
            "green_vico_hat", "window", "kernel_T", "vg_full", "spectrum", "solve_fft",
            "solve_direct", "solve", "analytic", "num_threads", "set_num_threads", "dst1", "trig1_3d",
            "field_kernel", "solve_field_fft", "field_spectrum", "solve_field_direct", "solve_field",
-           "kernel_T3", "solve_fft3", "spectrum3", "solve_direct3", "solve3"]
+           "kernel_T3", "solve_fft3", "spectrum3", "solve_direct3", "solve3", "field_kernel3",
+           "solve_field_fft3", "solve_field_direct3", "solve_field3"]
 

@@ -96,3 +96,16 @@ def gaussian_potential3(n, L, sigma=0.05, centre=(0.0, 0.0, 0.0), weight=1.0):
     out[~small] = erf(rr / (np.sqrt(2.0) * sigma)) / (4.0 * np.pi * rr)
     out[small] = np.sqrt(2.0 / np.pi) / (4.0 * np.pi * sigma)
     return weight * out
+
+
+def gaussian_field3(n, L, sigma=0.05, centre=(0.0, 0.0, 0.0), weight=1.0):
+    """gaussian_field on a non-cubic box; (E_x, E_y, E_z), shape (n_z, n_y, n_x)."""
+    shp = (n[2], n[1], n[0])
+    z = np.broadcast_to(cell_centres(n[2], L[2])[:, None, None] - centre[2], shp)
+    y = np.broadcast_to(cell_centres(n[1], L[1])[None, :, None] - centre[1], shp)
+    x = np.broadcast_to(cell_centres(n[0], L[0])[None, None, :] - centre[0], shp)
+    r = np.sqrt(x * x + y * y + z * z)
+    s = r / sigma
+    q = erf(s / np.sqrt(2.0)) - np.sqrt(2.0 / np.pi) * s * np.exp(-0.5 * s * s)
+    er_over_r = np.where(r > 1e-12, q / (4.0 * np.pi * np.maximum(r, 1e-300) ** 3), 0.0)
+    return tuple(weight * er_over_r * d for d in (x, y, z))

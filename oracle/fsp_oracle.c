@@ -33,6 +33,8 @@
  *                        spacings h_x, h_y, h_z (the non-cubic grids the
  *                        paper's weak-scaling runs use, Sec. 3.2); the window
  *                        is alpha times the box diagonal.
+ *   - orc_field_kernel3, orc_solve_field_fft3, orc_solve_field_direct3 : the
+ *                        field on those boxes.
  *   - orc_dst1_1d, orc_trig1_3d, orc_field_kernel, orc_solve_field_fft,
  *     orc_field_spectrum, orc_solve_field_direct : the field E = -grad phi of
  *                        Appendix B (Eq. efield), as the convolution of rho
@@ -827,6 +829,147 @@ void orc_solve_direct3(const int *n, const double *h, const double *T, const dou
                 const double *rrow = rho + ((size_t)jz * n[1] + jy) * n[0];
                 for (int jx = 0; jx < n[0]; ++jx) {
                     double t = Trow[abs(ix - jx)] * rrow[jx];
+                    double s = sum + t;
+                    if (fabs(sum) >= fabs(t))
+                        comp += (sum - s) + t;
+                    else
+                        comp += (t - s) + sum;
+                    sum = s;
+                }
+            }
+        out[p] = h[0] * h[1] * h[2] * (sum + comp);
+    }
+}
+
+/* ------------------------------------------- the field, non-cubic boxes -- */
+/*
+ * Field kernel F_a[m] = -dG/dx_a at (m_x h_x, m_y h_y, m_z h_z), m in the
+ * (n_x+1, n_y+1, n_z+1) octant, for a box of n cells with spacings h (the
+ * readings of orc_field_kernel, per axis):
+ *   HE:     m_a h_a / (4 pi |r|^3), F_a[0] = 0.
+ *   VG:     the inverse DFT of -i k_a G_L on the (4n_x, 4n_y, 4n_z) grid, the
+ *           Nyquist plane j_a = -2n_a at zero, over prod_a (4 n_a h_a), real.
+ *   VG-DCT: the octant samples k_a G_L, DST-I along a and DCT-I along the
+ *           others, over prod_a (4 n_a h_a).
+ * The window is alpha |(L_x, L_y, L_z)| as in orc_kernel_T3.
+ */
+void orc_field_kernel3(int algo, int a, const int *n, const double *h, double alpha, double *F) {
+    int k[3] = {n[0] + 1, n[1] + 1, n[2] + 1};
+    double Lb[3] = {n[0] * h[0], n[1] * h[1], n[2] * h[2]};
+    double Lt = alpha * sqrt(Lb[0] * Lb[0] + Lb[1] * Lb[1] + Lb[2] * Lb[2]);
+    if (algo == ORC_HE) {
+        for (int z = 0; z < k[2]; ++z)
+            for (int y = 0; y < k[1]; ++y)
+                for (int x = 0; x < k[0]; ++x) {
+                    double r[3] = {x * h[0], y * h[1], z * h[2]};
+                    double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                    F[((size_t)z * k[1] + y) * k[0] + x] = (x | y | z) ? r[a] / (4.0 * ORC_PI * r2 * sqrt(r2)) : 0.0;
+                }
+    } else if (algo == ORC_VG) {
+        int m[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
+        size_t tot = (size_t)m[0] * m[1] * m[2];
+        cplx *g = (cplx *)malloc(sizeof(cplx) * tot);
+        double dk[3];
+        for (int c = 0; c < 3; ++c) dk[c] = 2.0 * ORC_PI / ((double)m[c] * h[c]);
+#pragma omp parallel for schedule(static)
+        for (long long idx = 0; idx < (long long)tot; ++idx) {
+            int s3[3] = {(int)(idx % m[0]), (int)((idx / m[0]) % m[1]), (int)(idx / ((long long)m[0] * m[1]))};
+            int j[3];
+            double k2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                j[c] = s3[c] < 2 * n[c] ? s3[c] : s3[c] - m[c];
+                k2 += (dk[c] * j[c]) * (dk[c] * j[c]);
+            }
+            double ka = j[a] == -2 * n[a] ? 0.0 : dk[a] * j[a];
+            g[idx] = -I * ka * orc_green_vico_hat(sqrt(k2), Lt);
+        }
+        orc_fft3d(m[0], m[1], m[2], g, +1);
+        double scale = 1.0 / (((double)m[0] * h[0]) * ((double)m[1] * h[1]) * ((double)m[2] * h[2]));
+        for (int z = 0; z < k[2]; ++z)
+            for (int y = 0; y < k[1]; ++y)
+                for (int x = 0; x < k[0]; ++x)
+                    F[((size_t)z * k[1] + y) * k[0] + x] = creal(g[((size_t)z * m[1] + y) * m[0] + x]) * scale;
+        free(g);
+    } else {
+        int M[3] = {2 * n[0], 2 * n[1], 2 * n[2]}, q[3] = {M[0] + 1, M[1] + 1, M[2] + 1};
+        double dk[3];
+        for (int c = 0; c < 3; ++c) dk[c] = 2.0 * ORC_PI / (4.0 * n[c] * h[c]);
+        double *g = (double *)malloc(sizeof(double) * (size_t)q[0] * q[1] * q[2]);
+        for (int z = 0; z < q[2]; ++z)
+            for (int y = 0; y < q[1]; ++y)
+                for (int x = 0; x < q[0]; ++x) {
+                    double kk[3] = {dk[0] * x, dk[1] * y, dk[2] * z};
+                    g[((size_t)z * q[1] + y) * q[0] + x] =
+                        kk[a] * orc_green_vico_hat(sqrt(kk[0] * kk[0] + kk[1] * kk[1] + kk[2] * kk[2]), Lt);
+                }
+        double *t1 = (double *)malloc(sizeof(double) * (size_t)k[0] * q[1] * q[2]);
+        double *t2 = (double *)malloc(sizeof(double) * (size_t)k[0] * k[1] * q[2]);
+        axis_trig(M[0], n[0], a == 0, 0, q[0], q[1], q[2], g, t1);
+        axis_trig(M[1], n[1], a == 1, 1, k[0], q[1], q[2], t1, t2);
+        axis_trig(M[2], n[2], a == 2, 2, k[0], k[1], q[2], t2, F);
+        double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[1] * h[1]) * (4.0 * n[2] * h[2]));
+        for (size_t i = 0; i < (size_t)k[0] * k[1] * k[2]; ++i) F[i] *= scale;
+        free(t2);
+        free(t1);
+        free(g);
+    }
+}
+
+/* F_2 on the (2n_x, 2n_y, 2n_z) doubled grid, odd in axis a (odd_sign). */
+static void field_doubled3(const int *n, int a, const double *F, cplx *g2) {
+    int d[3] = {2 * n[0], 2 * n[1], 2 * n[2]}, k[3] = {n[0] + 1, n[1] + 1, n[2] + 1};
+    for (int z = 0; z < d[2]; ++z)
+        for (int y = 0; y < d[1]; ++y)
+            for (int x = 0; x < d[0]; ++x) {
+                int m[3] = {x, y, z};
+                g2[((size_t)z * d[1] + y) * d[0] + x] =
+                    odd_sign(m[a], n[a]) * F[((size_t)fold2(z, n[2]) * k[1] + fold2(y, n[1])) * k[0] + fold2(x, n[0])];
+            }
+}
+
+/* E_a = h_x h_y h_z sum_j F_a[i - j] rho_j through the full doubled grid. */
+void orc_solve_field_fft3(const int *n, const double *h, int a, const double *F, const double *rho, double *E) {
+    int d[3] = {2 * n[0], 2 * n[1], 2 * n[2]};
+    size_t tot = (size_t)d[0] * d[1] * d[2];
+    cplx *r2 = (cplx *)calloc(tot, sizeof(cplx));
+    cplx *g2 = (cplx *)malloc(sizeof(cplx) * tot);
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x)
+                r2[((size_t)z * d[1] + y) * d[0] + x] = rho[((size_t)z * n[1] + y) * n[0] + x];
+    field_doubled3(n, a, F, g2);
+    orc_fft3d(d[0], d[1], d[2], r2, -1);
+    orc_fft3d(d[0], d[1], d[2], g2, -1);
+    for (size_t i = 0; i < tot; ++i) r2[i] *= g2[i];
+    orc_fft3d(d[0], d[1], d[2], r2, +1);
+    double scale = h[0] * h[1] * h[2] / (double)tot;
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x)
+                E[((size_t)z * n[1] + y) * n[0] + x] = creal(r2[((size_t)z * d[1] + y) * d[0] + x]) * scale;
+    free(g2);
+    free(r2);
+}
+
+/* E_a[i] = h_x h_y h_z sum_j sgn(i_a - j_a) F_a[|i - j|] rho_j (Neumaier). */
+void orc_solve_field_direct3(const int *n, const double *h, int a, const double *F, const double *rho,
+                             const long long *pts, long long npts, double *out) {
+    int k[3] = {n[0] + 1, n[1] + 1, n[2] + 1};
+    long long total = pts ? npts : (long long)n[0] * n[1] * n[2];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long p = 0; p < total; ++p) {
+        long long i = pts ? pts[p] : p;
+        int ii[3] = {(int)(i % n[0]), (int)((i / n[0]) % n[1]), (int)(i / ((long long)n[0] * n[1]))};
+        double sum = 0.0, comp = 0.0;
+        for (int jz = 0; jz < n[2]; ++jz)
+            for (int jy = 0; jy < n[1]; ++jy) {
+                const double *Frow = F + ((size_t)abs(ii[2] - jz) * k[1] + abs(ii[1] - jy)) * k[0];
+                const double *rrow = rho + ((size_t)jz * n[1] + jy) * n[0];
+                for (int jx = 0; jx < n[0]; ++jx) {
+                    int jj[3] = {jx, jy, jz};
+                    int dd = ii[a] - jj[a];
+                    double sg = dd > 0 ? 1.0 : (dd < 0 ? -1.0 : 0.0);
+                    double t = sg * Frow[abs(ii[0] - jx)] * rrow[jx];
                     double s = sum + t;
                     if (fabs(sum) >= fabs(t))
                         comp += (sum - s) + t;

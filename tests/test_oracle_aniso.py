@@ -98,3 +98,63 @@ def test_far_field_pins_the_window(orc):
     # (beyond 3 min L_a: aliased by the 4n periodisation) both fail
     assert _far_field(orc, orc.ALPHA * np.sqrt(3) * 1.0 / np.sqrt(6)) > 0.1
     assert _far_field(orc, orc.ALPHA * np.sqrt(3) * 2.0 / np.sqrt(6)) > 0.1
+
+
+# ---- the field E = -grad phi on non-cubic boxes (Appendix B, Eq. efield)
+
+@pytest.mark.parametrize("algo", ["he", "vg", "vg_dct"])
+def test_field_cube_equals_cubic_oracle(orc, algo):
+    for a in range(3):
+        F = orc.field_kernel(algo, a, 6)
+        F3 = orc.field_kernel3(algo, a, (6, 6, 6), (1.0 / 6,) * 3)
+        np.testing.assert_allclose(F3, F, rtol=0, atol=1e-13 * np.abs(F).max())
+
+
+@pytest.mark.parametrize("n,h", SHAPES)
+def test_field_fft_equals_direct_and_two_routes(orc, n, h):
+    rho = I.random_field3(n, 8)
+    for a in range(3):
+        Fv, Fd = orc.field_kernel3("vg", a, n, h), orc.field_kernel3("vg_dct", a, n, h)
+        np.testing.assert_allclose(Fv, Fd, rtol=0, atol=1e-13 * np.abs(Fv).max())
+        for algo in ("he", "vg_dct"):
+            F = orc.field_kernel3(algo, a, n, h)
+            e1, e2 = orc.solve_field_fft3(F, a, rho, h), orc.solve_field_direct3(F, a, rho, h)
+            np.testing.assert_allclose(e1, e2, rtol=0, atol=1e-13 * np.abs(e2).max())
+
+
+def test_field_he_impulse_is_coulomb(orc):
+    n, h, j = (7, 5, 6), (0.1, 0.17, 0.13), (2, 4, 1)
+    rho = np.zeros((n[2], n[1], n[0]))
+    rho[j[2], j[1], j[0]] = 1.0 / (h[0] * h[1] * h[2])
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    d = [(x - j[0]) * h[0], (y - j[1]) * h[1], (z - j[2]) * h[2]]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    for a in range(3):
+        E = orc.solve_field_fft3(orc.field_kernel3("he", a, n, h), a, rho, h)
+        want = (r > 0) * d[a] / (4 * np.pi * np.where(r > 0, r, 1.0) ** 3)
+        np.testing.assert_allclose(E, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+def test_field_vg_gaussian_on_noncubic_box(orc):
+    n, L = (40, 32, 48), (1.0, 0.8, 1.2)
+    h = tuple(L[a] / n[a] for a in range(3))
+    E = orc.solve_field3("vg_dct", I.gaussian3(n, L), h)
+    ex = A.gaussian_field3(n, L)
+    err = max(np.abs(E[a] - ex[a]).max() for a in range(3)) / max(np.abs(ex[a]).max() for a in range(3))
+    assert err < 1e-8, err
+
+
+def test_field_is_minus_gradient_on_noncubic_box(orc):
+    """E_a against the fourth-order central difference (spacing h_a) of the
+    oracle's own potential, smooth Gaussian (sigma = 0.12: the difference's
+    own truncation error stays near 1e-3 at h_y = 0.0375), interior points."""
+    n, L = (32, 24, 40), (1.0, 0.9, 1.25)
+    h = tuple(L[a] / n[a] for a in range(3))
+    rho = I.gaussian3(n, L, 0.12)
+    phi = orc.solve3("vg_dct", rho, h)
+    E = orc.solve_field3("vg_dct", rho, h)
+    for a, ax in ((0, 2), (1, 1), (2, 0)):
+        p = np.moveaxis(phi, ax, 0)
+        d = (-p[4:] + 8 * p[3:-1] - 8 * p[1:-3] + p[:-4]) / (12 * h[a])
+        e = np.moveaxis(E[a], ax, 0)[2:-2]
+        assert np.abs(e + d).max() < 2e-3 * np.abs(e).max(), (a, np.abs(e + d).max() / np.abs(e).max())

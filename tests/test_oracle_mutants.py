@@ -190,6 +190,9 @@ ANISO_MUTANTS = [
      "T[((size_t)fold2(z, n[2]) * k[1] + fold2(y, n[0])) * k[0] + fold2(x, n[0])];"),
     ("solve3_scale", "double scale = h[0] * h[1] * h[2] / (double)tot;\n    for (int z = 0; z < n[2]; ++z)",
      "double scale = h[0] * h[0] * h[0] / (double)tot;\n    for (int z = 0; z < n[2]; ++z)"),
+    ("he_field3_spacing", "double r[3] = {x * h[0], y * h[1], z * h[2]};", "double r[3] = {x * h[0], y * h[0], z * h[2]};"),
+    ("field_doubled3_odd_axis", "odd_sign(m[a], n[a]) * F[((size_t)fold2(z, n[2])", "odd_sign(m[a], n[0]) * F[((size_t)fold2(z, n[2])"),
+    ("vg_field3_ka_axis", "double ka = j[a] == -2 * n[a] ? 0.0 : dk[a] * j[a];", "double ka = j[a] == -2 * n[a] ? 0.0 : dk[0] * j[a];"),
     ("vgdct3_scale_axis", "double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[1] * h[1]) * (4.0 * n[2] * h[2]));",
      "double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[0] * h[1]) * (4.0 * n[2] * h[2]));"),
 ]
@@ -237,6 +240,30 @@ def _aniso_pins(orc):
     xx = I.cell_centres(nf[0], Lf[0])[None, None, :] - c[0]
     far = np.sqrt(xx * xx + yy * yy + zz * zz) > 1.2
     res["far_field"] = float(np.max(np.abs(phi[far] - ex[far]) / ex[far])) < 1e-2
+    # the field on a non-cubic box
+    nf3, hf3 = (6, 4, 5), (0.2, 0.3, 0.25)
+    rr = I.random_field3(nf3, 6)
+    ok_routes, ok_direct = True, True
+    for a in range(3):
+        Fv, Fd = orc.field_kernel3("vg", a, nf3, hf3), orc.field_kernel3("vg_dct", a, nf3, hf3)
+        ok_routes = ok_routes and np.allclose(Fv, Fd, rtol=0, atol=1e-12 * np.abs(Fv).max())
+        for algo in ("he", "vg_dct"):
+            F = orc.field_kernel3(algo, a, nf3, hf3)
+            e2 = orc.solve_field_direct3(F, a, rr, hf3)
+            ok_direct = ok_direct and np.allclose(orc.solve_field_fft3(F, a, rr, hf3), e2, rtol=0,
+                                                  atol=1e-12 * np.abs(e2).max())
+    res["field_vg_two_routes"] = ok_routes
+    res["field_fft_eq_direct"] = ok_direct
+    ni, hi, j = (7, 5, 6), (0.1, 0.17, 0.13), (2, 4, 1)
+    rho = np.zeros((ni[2], ni[1], ni[0]))
+    rho[j[2], j[1], j[0]] = 1.0 / (hi[0] * hi[1] * hi[2])
+    z, y, x = np.meshgrid(np.arange(ni[2]), np.arange(ni[1]), np.arange(ni[0]), indexing="ij")
+    d = [(x - j[0]) * hi[0], (y - j[1]) * hi[1], (z - j[2]) * hi[2]]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    res["field_coulomb"] = all(
+        np.allclose(orc.solve_field_fft3(orc.field_kernel3("he", a, ni, hi), a, rho, hi),
+                    (r > 0) * d[a] / (4 * np.pi * np.where(r > 0, r, 1.0) ** 3), rtol=1e-10, atol=1e-10)
+        for a in range(3))
     return res
 
 

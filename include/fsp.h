@@ -117,8 +117,10 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
  * 3 nz ny P complex values (P = nx+1 rounded up to 16), the spectrum
  * (nz+1)(ny+1)P reals.  fsp_solve, fsp_solve_host(_many), fsp_plan_sync,
  * fsp_plan_set_timing, fsp_plan_spectrum ((nz+1)(ny+1)(nx+1) doubles) and
- * fsp_plan_destroy accept the plan; field solves and batches
- * (fsp_plan_field_init, fsp_batch_create) return FSP_EUNSUPPORTED for it.
+ * fsp_plan_destroy accept the plan, and so do fsp_plan_field_init and
+ * fsp_solve_field (the field kernels per axis, F_a = m_a h_a / (4 pi |r|^3)
+ * for HE and the octant route with the box's window for VG); batches
+ * (fsp_batch_create) return FSP_EUNSUPPORTED for it.
  */
 fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double hx, double hy, double hz,
                                  fsp_algo algo, fsp_dtype dtype, fsp_stream stream);

@@ -22,6 +22,7 @@
 
 #include "../../include/fsp.h"
 #include "batch.h"
+#include "fast_field.h"
 #include "df.cuh"
 #include "fast.h"
 #include "greens.h"
@@ -386,6 +387,22 @@ fsp_status enqueue_field_kernel(int N, double L, fsp_algo algo, int axis, double
     return cuda_status(launch_scale(f_dev, (long long)k1 * k1 * k1, scale, s));
 }
 
+// The same on a non-cubic box (per-axis sizes and spacings, window
+// 1.1 |(L_x, L_y, L_z)|), (n_z+1)(n_y+1)(n_x+1) values.
+fsp_status enqueue_field_kernel3(const int *nn, const double *hh, fsp_algo algo, int axis, double *f_dev, cudaStream_t s,
+                                 Temps &tmp) {
+    if (algo == FSP_HE) return cuda_status(launch_he_F3(f_dev, nn, hh, axis, s));
+    const double Lb[3] = {nn[0] * hh[0], nn[1] * hh[1], nn[2] * hh[2]};
+    const double Lt = kAlpha * std::sqrt(Lb[0] * Lb[0] + Lb[1] * Lb[1] + Lb[2] * Lb[2]);
+    fsp_status st;
+    const size_t q = (size_t)(2 * nn[0] + 1) * (2 * nn[1] + 1) * (2 * nn[2] + 1);
+    if ((st = alloc_or_nomem(tmp.g, sizeof(double) * q)) != FSP_OK) return st;
+    FSP_TRY_CUDA(launch_vg_sample_octant_grad3((double *)tmp.g.p, nn, hh, Lt, axis, s));
+    if ((st = enqueue_octant_transform3(nn, axis, (double *)tmp.g.p, f_dev, s, tmp)) != FSP_OK) return st;
+    const double scale = 1.0 / ((4.0 * nn[0] * hh[0]) * (4.0 * nn[1] * hh[1]) * (4.0 * nn[2] * hh[2]));
+    return cuda_status(launch_scale(f_dev, (long long)(nn[0] + 1) * (nn[1] + 1) * (nn[2] + 1), scale, s));
+}
+
 fsp_status validate_size(int N, double L, fsp_algo algo) {
     if (N < 2 || N > kMaxN) return N < 2 ? FSP_EINVAL : FSP_EUNSUPPORTED;
     if (!(L > 0.0) || !std::isfinite(L)) return FSP_EINVAL;
@@ -603,7 +620,83 @@ cudaError_t enqueue_field_generic(const fsp_plan *p, const void *rho, void *cons
     return cudaSuccess;
 }
 
+// The field on a non-cubic box: P1, P2 once, then per output P3 (W2 -> W3,
+// S folded at n_z in z and n_y in k_y), P4, P5; generic engine or the
+// specialised kernels with runtime strides.
+template <typename T>
+cudaError_t enqueue_field_aniso(const fsp_plan *p, const void *rho, void *const out[4], cudaStream_t s) {
+    const int nx = p->n3[0], ny = p->n3[1], nz = p->n3[2];
+    const long long P = p->P;
+    cudaError_t e;
+    if (p->fast) {
+        fast::RowArgs r{};
+        r.x = rho, r.c = p->W1, r.x_row = nx, r.c_row = P, r.nrows = ny * nz, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+        if ((e = fast::p1<T>(nx, r, s)) != cudaSuccess) return e;
+        fast::ColArgs a{};
+        a.nlines = nx + 1;
+        a.tw = p->tw_y, a.in = p->W1, a.out = p->W2;
+        a.in_pos = P, a.in_batch = (long long)ny * P, a.out_pos = P, a.out_batch = 2LL * ny * P;
+        if ((e = fast::col_rg<T>(fast::COL_FWD, 2 * ny, a, nz, s)) != cudaSuccess) return e;
+        for (int c = 3; c >= 0; --c) {
+            if (!out[c]) continue;
+            fast::ColArgs b = a;
+            b.tw = p->tw_z, b.in = p->W2, b.out = p->W3;
+            b.in_pos = b.out_pos = 2LL * ny * P, b.in_batch = b.out_batch = P;
+            b.S = c == 3 ? p->S : p->SF[c], b.s_pos = (long long)(ny + 1) * P, b.s_batch = P, b.half = nz, b.half_b = ny;
+            b.odd = c == 3 ? 0 : kP3Odd[c];
+            if ((e = c == 3 ? fast::col_rg<T>(fast::COL_FMI, 2 * nz, b, 2 * ny, s)
+                            : fast::p3_odd_rg<T>(2 * nz, b, 2 * ny, s)) != cudaSuccess)
+                return e;
+            b.tw = p->tw_y, b.in = p->W3, b.out = p->W1, b.odd = 0;
+            b.in_pos = P, b.in_batch = 2LL * ny * P, b.out_pos = P, b.out_batch = (long long)ny * P;
+            if ((e = fast::col_rg<T>(fast::COL_INV, 2 * ny, b, nz, s)) != cudaSuccess) return e;
+            r.x = out[c];
+            if ((e = fast::p5<T>(nx, r, s)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    if constexpr (std::is_same<T, df>::value) {
+        return cudaErrorInvalidValue;  // double-float plans always have the specialised kernels
+    } else {
+        RowsArgs r{};
+        r.x = rho, r.c = p->W1, r.x_row = nx, r.c_row = P, r.N = nx, r.nrows = ny * nz;
+        r.lgL = p->row.lgL, r.tpl = p->row.tpl, r.st = p->row.st, r.tw = p->tw_n, r.tw2 = p->tw_2n;
+        if ((e = launch_r2c_rows<T>(r, s)) != cudaSuccess) return e;
+        LinesArgs a{};
+        a.st = p->col.st, a.tpl = p->col.tpl, a.lgL = p->col.lgL, a.tw = p->tw_y;
+        a.in = p->W1, a.out = p->W2;
+        a.in_pos = P, a.in_line = 1, a.in_batch = (long long)ny * P;
+        a.out_pos = P, a.out_line = 1, a.out_batch = 2LL * ny * P;
+        a.n_in = ny, a.n_out = 2 * ny, a.nlines = nx + 1, a.nbatch = nz;
+        if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD>(a, s)) != cudaSuccess) return e;
+        for (int c = 3; c >= 0; --c) {
+            if (!out[c]) continue;
+            LinesArgs b = a;
+            b.st = p->colz.st, b.tpl = p->colz.tpl, b.lgL = p->colz.lgL, b.tw = p->tw_z;
+            b.in = p->W2, b.out = p->W3;
+            b.in_pos = b.out_pos = 2LL * ny * P, b.in_batch = b.out_batch = P;
+            b.n_in = nz, b.n_out = nz, b.nbatch = 2 * ny;
+            b.S = c == 3 ? p->S : p->SF[c], b.s_pos = (long long)(ny + 1) * P, b.s_batch = P, b.half = nz, b.half_b = ny;
+            b.odd = c == 3 ? 0 : kP3Odd[c];
+            if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_FWD_MUL_INV>(b, s)) != cudaSuccess) return e;
+            b.st = p->col.st, b.tpl = p->col.tpl, b.lgL = p->col.lgL, b.tw = p->tw_y;
+            b.in = p->W3, b.out = p->W1, b.odd = 0, b.half_b = 0;
+            b.in_pos = P, b.in_batch = 2LL * ny * P;
+            b.out_pos = P, b.out_batch = (long long)ny * P;
+            b.n_in = 2 * ny, b.n_out = ny, b.nbatch = nz;
+            if ((e = launch_lines<T, IN_CPLX, OUT_CPLX, M_INV>(b, s)) != cudaSuccess) return e;
+            r.x = out[c];
+            if ((e = launch_c2r_rows<T>(r, s)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+}
+
 cudaError_t enqueue_field(const fsp_plan *p, const void *rho, void *const out[4], cudaStream_t s) {
+    if (p->aniso)
+        return p->dtype == FSP_F64      ? enqueue_field_aniso<double>(p, rho, out, s)
+               : p->dtype == FSP_F64_DF ? enqueue_field_aniso<df>(p, rho, out, s)
+                                        : enqueue_field_aniso<float>(p, rho, out, s);
     if (p->dtype == FSP_F64_DF) return enqueue_field_fast<df>(p, rho, out, s);
     if (p->fast)
         return p->dtype == FSP_F64 ? enqueue_field_fast<double>(p, rho, out, s)
@@ -953,7 +1046,6 @@ fsp_status fsp_solve(fsp_plan *plan, const void *rho, void *phi, fsp_stream stre
 fsp_status fsp_plan_field_init(fsp_plan *plan, fsp_stream stream) {
     if (!plan_live(plan)) return FSP_EINVAL;
     if (!plan->W1) return FSP_EINVAL;
-    if (plan->aniso) return FSP_EUNSUPPORTED;  // field solves: cubic boxes
     if (plan->W3) return FSP_OK;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
@@ -961,35 +1053,41 @@ fsp_status fsp_plan_field_init(fsp_plan *plan, fsp_stream stream) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();
     const int N = plan->N;
-    const size_t k1 = N + 1;
-    const size_t sbytes = k1 * k1 * plan->P * plan->rsize;
-    const size_t w2 = 2 * (size_t)N * N * plan->P * 2 * plan->rsize;
+    // the box: cubic, or the plan's non-cubic sizes and spacings
+    const int nn[3] = {plan->aniso ? plan->n3[0] : N, plan->aniso ? plan->n3[1] : N, plan->aniso ? plan->n3[2] : N};
+    const double hb[3] = {plan->aniso ? plan->h3[0] : plan->h, plan->aniso ? plan->h3[1] : plan->h,
+                          plan->aniso ? plan->h3[2] : plan->h};
+    const int kx = nn[0] + 1;
+    const long long rows = (long long)(nn[1] + 1) * (nn[2] + 1);
+    const size_t sbytes = (size_t)rows * plan->P * plan->rsize;
+    const size_t w2 = 2 * (size_t)nn[2] * nn[1] * plan->P * 2 * plan->rsize;
     DevBuf bs[3], bw;
     fsp_status st;
     for (auto &b : bs)
         if ((st = alloc_or_nomem(b, sbytes)) != FSP_OK) return st;
     if ((st = alloc_or_nomem(bw, w2)) != FSP_OK) return st;
-    const double hh = plan->h;
-    const double scale = hh * hh * hh / ((2.0 * N) * (2.0 * N) * (2.0 * N));
+    const double scale = hb[0] * hb[1] * hb[2] / ((2.0 * nn[0]) * (2.0 * nn[1]) * (2.0 * nn[2]));
     for (int axis = 0; axis < 3; ++axis) {
         // plan-time field spectrum S_a = h^3 / (2N)^3 * DST/DCT of F_a, FP64,
         // rounded to the plan's type; each component's temporaries live
         // until its work has finished
         Temps tmp, tw;
         DevBuf Fd;
-        if ((st = alloc_or_nomem(Fd, sizeof(double) * k1 * k1 * k1)) != FSP_OK) return st;
-        if ((st = enqueue_field_kernel(N, plan->L, plan->algo, axis, (double *)Fd.p, s, tmp)) != FSP_OK) {
+        if ((st = alloc_or_nomem(Fd, sizeof(double) * (size_t)kx * rows)) != FSP_OK) return st;
+        st = plan->aniso ? enqueue_field_kernel3(nn, hb, plan->algo, axis, (double *)Fd.p, s, tmp)
+                         : enqueue_field_kernel(N, plan->L, plan->algo, axis, (double *)Fd.p, s, tmp);
+        if (st != FSP_OK) {
             cudaStreamSynchronize(s);
             return st;
         }
-        if ((st = enqueue_trig_spectrum(N, axis, (double *)Fd.p, s, tw)) != FSP_OK) {
+        if ((st = enqueue_trig_spectrum3(nn, axis, (double *)Fd.p, s, tw)) != FSP_OK) {
             cudaStreamSynchronize(s);
             return st;
         }
-        cudaError_t e = plan->dtype == FSP_F64 ? launch_store_S<double>((double *)Fd.p, bs[axis].p, N, plan->P, scale, s)
-                        : plan->dtype == FSP_F64_DF
-                            ? launch_store_S<df>((double *)Fd.p, bs[axis].p, N, plan->P, scale, s)
-                            : launch_store_S<float>((double *)Fd.p, bs[axis].p, N, plan->P, scale, s);
+        cudaError_t e =
+            plan->dtype == FSP_F64      ? launch_store_S3<double>((double *)Fd.p, bs[axis].p, kx, rows, plan->P, scale, s)
+            : plan->dtype == FSP_F64_DF ? launch_store_S3<df>((double *)Fd.p, bs[axis].p, kx, rows, plan->P, scale, s)
+                                        : launch_store_S3<float>((double *)Fd.p, bs[axis].p, kx, rows, plan->P, scale, s);
         if (cudaStreamSynchronize(s) != cudaSuccess || e != cudaSuccess) return FSP_ECUDA;
     }
     for (int axis = 0; axis < 3; ++axis) plan->SF[axis] = bs[axis].release();

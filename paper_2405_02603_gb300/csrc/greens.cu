@@ -130,6 +130,31 @@ __global__ void k_vg_sample_full3(double2 *g, int mx, int my, int mz, double dkx
     }
 }
 
+// Field kernels on a non-cubic box: F_a[m] = m_a h_a / (4 pi |r|^3), r =
+// (m_x h_x, m_y h_y, m_z h_z), F_a[0] = 0; and the octant of k_a G_L(|k|),
+// k = (dk_x j_x, dk_y j_y, dk_z j_z).
+__global__ void k_he_F3(double *F, int kx, int ky, int kz, double hx, double hy, double hz, int a) {
+    const long long tot = (long long)kx * ky * kz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % kx), y = (int)((i / kx) % ky), z = (int)(i / ((long long)kx * ky));
+        const double rx = x * hx, ry = y * hy, rz = z * hz;
+        const double ra = a == 0 ? rx : (a == 1 ? ry : rz);
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        F[i] = (x | y | z) ? inv4pi() * ra / (r2 * sqrt(r2)) : 0.0;
+    }
+}
+
+__global__ void k_vg_sample_octant_grad3(double *g, int qx, int qy, int qz, double dkx, double dky, double dkz, double Lt,
+                                         int a) {
+    const long long tot = (long long)qx * qy * qz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % qx), y = (int)((i / qx) % qy), z = (int)(i / ((long long)qx * qy));
+        const double kx = dkx * x, ky = dky * y, kz = dkz * z;
+        const double ka = a == 0 ? kx : (a == 1 ? ky : kz);
+        g[i] = ka * green_vico_hat(sqrt(kx * kx + ky * ky + kz * kz), Lt);
+    }
+}
+
 __global__ void k_scale(double *a, long long n, double s) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] *= s;
@@ -200,6 +225,21 @@ cudaError_t launch_vg_sample_octant_grad(double *g, int N, double h, double Lt, 
 
 cudaError_t launch_scale(double *a, long long n, double sc, cudaStream_t s) {
     k_scale<<<grid_for(n), 256, 0, s>>>(a, n, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_he_F3(double *F, const int *n, const double *h, int a, cudaStream_t s) {
+    const long long tot = (long long)(n[0] + 1) * (n[1] + 1) * (n[2] + 1);
+    k_he_F3<<<grid_for(tot), 256, 0, s>>>(F, n[0] + 1, n[1] + 1, n[2] + 1, h[0], h[1], h[2], a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vg_sample_octant_grad3(double *g, const int *n, const double *h, double Lt, int a, cudaStream_t s) {
+    const int q[3] = {2 * n[0] + 1, 2 * n[1] + 1, 2 * n[2] + 1};
+    double dk[3];
+    for (int c = 0; c < 3; ++c) dk[c] = 6.283185307179586476925286766559 / (4.0 * n[c] * h[c]);
+    k_vg_sample_octant_grad3<<<grid_for((long long)q[0] * q[1] * q[2]), 256, 0, s>>>(g, q[0], q[1], q[2], dk[0], dk[1],
+                                                                                     dk[2], Lt, a);
     return cudaGetLastError();
 }
 

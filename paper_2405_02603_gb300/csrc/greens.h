@@ -16,6 +16,8 @@ template <typename T> cudaError_t launch_load_S(const void *S, double *Sd, int N
 cudaError_t launch_he_T3(double *T, const int *n, const double *h, cudaStream_t s);
 cudaError_t launch_vg_sample_octant3(double *g, const int *n, const double *h, double Lt, cudaStream_t s);
 cudaError_t launch_vg_sample_full3(void *g, const int *n, const double *h, double Lt, cudaStream_t s);
+cudaError_t launch_he_F3(double *F, const int *n, const double *h, int a, cudaStream_t s);
+cudaError_t launch_vg_sample_octant_grad3(double *g, const int *n, const double *h, double Lt, int a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_store_S3(const double *Sd, void *S, int kx, long long rows, int P, double scale, cudaStream_t s);
 template <typename T> cudaError_t launch_load_S3(const void *S, double *Sd, int kx, long long rows, int P, cudaStream_t s);

@@ -111,11 +111,9 @@ def test_cube_through_aniso_is_the_cubic_plan(fsp):
     b.close()
 
 
-def test_aniso_plan_rejects_field_and_batch(fsp):
+def test_aniso_plan_rejects_batch(fsp):
     import torch
     p = fsp.Plan((8, 12, 16), (1.0, 1.0, 1.0), "he", "f32")
-    with pytest.raises(fsp.FspError):
-        p.field_init()
     rho = torch.zeros(p.npoints, dtype=torch.float32, device="cuda")
     with pytest.raises(fsp.FspError):
         fsp.solve_batched([p], [rho], [torch.empty_like(rho)])

@@ -137,3 +137,48 @@ def test_field_n256_sampled_direct_sum(fsp, orc, dtype):
         print("N=256 vg %s field component %d sampled E_max = %.3e" % (dtype, a, err))
         assert err <= TOL[dtype]
     p.close()
+
+
+# ---- non-cubic boxes
+
+ANISO_FIELD = [((12, 20, 9), (1.0, 1.25, 0.9), ["f64", "f32"]), ((24, 24, 48), (1.0, 1.0, 2.0), ["f64", "f32"]),
+               ((32, 64, 128), (1.0, 1.0, 2.0), ["f64", "f32", "f64df"]),
+               ((64, 32, 32), (1.2, 1.0, 0.8), ["f64", "f32", "f64df"])]
+
+
+@pytest.mark.parametrize("algo", ["he", "vg_dct"])
+@pytest.mark.parametrize("n,L,dtypes", ANISO_FIELD)
+def test_field_noncubic(fsp, orc, n, L, dtypes, algo):
+    """Every component on non-cubic boxes (generic engine for the first two,
+    the specialised kernels with runtime strides for the power-of-two ones)
+    against the oracle's doubled-grid FFT; phi beside it bitwise that of
+    fsp_solve."""
+    h = tuple(L[a] / n[a] for a in range(3))
+    rho = I.gaussian_mixture3(n, L, seed=17 + n[0]).astype(np.float32).astype(np.float64)
+    F = [orc.field_kernel3(algo, a, n, h) for a in range(3)]
+    refs = [orc.solve_field_fft3(F[a], a, rho, h) for a in range(3)]
+    for dtype in dtypes:
+        p = fsp.Plan(n, L, algo, dtype)
+        out = p.solve_field(to_dev(rho, dtype), with_phi=True)
+        errs = [e_max(out[a].cpu().numpy(), refs[a]) for a in range(3)]
+        print("field %s %s %s fast=%s E_max %s" % (n, algo, dtype, p.fast_path, ["%.2e" % e for e in errs]))
+        assert max(errs) <= TOL[dtype], errs
+        assert bool((out[3] == p.solve(to_dev(rho, dtype))).all())
+        p.close()
+
+
+def test_field_noncubic_impulse_is_coulomb(fsp):
+    n, L = (32, 64, 128), (1.0, 1.0, 2.0)
+    h = tuple(L[a] / n[a] for a in range(3))
+    j = (5, 40, 70)
+    rho = np.zeros((n[2], n[1], n[0]))
+    rho[j[2], j[1], j[0]] = 1.0 / (h[0] * h[1] * h[2])
+    p = fsp.Plan(n, L, "he", "f64")
+    E = [e.cpu().numpy() for e in p.solve_field(to_dev(rho))]
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    d = [(x - j[0]) * h[0], (y - j[1]) * h[1], (z - j[2]) * h[2]]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    for a in range(3):
+        want = (r > 0) * d[a] / (4 * np.pi * np.where(r > 0, r, 1.0) ** 3)
+        assert e_max(E[a], want) < 1e-12
+    p.close()

@@ -158,3 +158,15 @@ def test_field_is_minus_gradient_on_noncubic_box(orc):
         d = (-p[4:] + 8 * p[3:-1] - 8 * p[1:-3] + p[:-4]) / (12 * h[a])
         e = np.moveaxis(E[a], ax, 0)[2:-2]
         assert np.abs(e + d).max() < 2e-3 * np.abs(e).max(), (a, np.abs(e + d).max() / np.abs(e).max())
+
+
+@pytest.mark.parametrize("algo", ["he", "vg_dct"])
+@pytest.mark.parametrize("n,h", SHAPES)
+def test_spectrum3_is_dct1_of_kernel(orc, algo, n, h):
+    """The spectrum from the full doubled-grid FFT equals the type-I DCT of the
+    octant (scipy REDFT00 per axis) times h_x h_y h_z / (8 n_x n_y n_z): the
+    2n_a DFT of a sequence even about 0 and n_a."""
+    import scipy.fft as sf
+    T = orc.kernel_T3(algo, n, h)
+    want = sf.dctn(T, type=1) * h[0] * h[1] * h[2] / (8.0 * n[0] * n[1] * n[2])
+    np.testing.assert_allclose(orc.spectrum3(T, h), want, rtol=0, atol=1e-12 * np.abs(want).max())

@@ -30,24 +30,43 @@ __device__ __forceinline__ void lines_tile(const LinesArgs &a, int bx, long long
     const long long b = by;
     const int n = a.st.n;
 
-    // ---- load (with zero padding / even extension)
+    // ---- load (with zero padding / even extension); U loads of a thread are
+    // issued before their shared-memory stores, so that several are in flight
+    constexpr int U = 4;
     if (IN == IN_CPLX) {
         const C *in = reinterpret_cast<const C *>(a.in) + b * a.in_batch;
         const int cnt = L * a.n_in;
         if (a.in_line == 1) {
-            for (int idx = tid; idx < cnt; idx += nth) {
-                const int l = idx & lmask, p = idx >> a.lgL;
-                C v = C{T(0), T(0)};
-                if (line0 + l < a.nlines) v = ldw<COH>(in + ((long long)(line0 + l) + (long long)p * a.in_pos));
-                buf[p * ld + l] = v;
+            for (int base = tid; base < cnt; base += U * nth) {
+                C q[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = base + u * nth, l = idx & lmask, p = idx >> a.lgL;
+                    q[u] = C{T(0), T(0)};
+                    if (idx < cnt && line0 + l < a.nlines)
+                        q[u] = ldw<COH>(in + ((long long)(line0 + l) + (long long)p * a.in_pos));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = base + u * nth;
+                    if (idx < cnt) buf[(idx >> a.lgL) * ld + (idx & lmask)] = q[u];
+                }
             }
         } else {
-            for (int idx = tid; idx < cnt; idx += nth) {
-                const int p = idx % a.n_in, l = idx / a.n_in;
-                C v = C{T(0), T(0)};
-                if (line0 + l < a.nlines)
-                    v = ldw<COH>(in + ((long long)(line0 + l) * a.in_line + (long long)p * a.in_pos));
-                buf[p * ld + l] = v;
+            for (int base = tid; base < cnt; base += U * nth) {
+                C q[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = base + u * nth, p = idx % a.n_in, l = idx / a.n_in;
+                    q[u] = C{T(0), T(0)};
+                    if (idx < cnt && line0 + l < a.nlines)
+                        q[u] = ldw<COH>(in + ((long long)(line0 + l) * a.in_line + (long long)p * a.in_pos));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = base + u * nth;
+                    if (idx < cnt) buf[(idx % a.n_in) * ld + idx / a.n_in] = q[u];
+                }
             }
         }
         const int zc = L * (n - a.n_in);
@@ -177,19 +196,28 @@ __device__ __forceinline__ void r2c_tile(const RowsArgs &a, int bx, unsigned cha
     const T *x = reinterpret_cast<const T *>(a.x);
 
     const int cnt = L * Mh;
-    for (int idx = tid; idx < cnt; idx += nth) {
-        const int m = idx % Mh, l = idx / Mh;
-        C v = C{T(0), T(0)};
-        if (row0 + l < a.nrows) {
-            const T *xr = x + (row0 + l) * a.x_row;
-            if ((N & 1) == 0) {
-                v = ldw<COH>(reinterpret_cast<const C *>(xr) + m);
-            } else {
-                v.x = ldw<COH>(xr + 2 * m);
-                v.y = (2 * m + 1 < N) ? ldw<COH>(xr + 2 * m + 1) : T(0);
+    constexpr int U = 4;  // loads in flight per thread
+    for (int base = tid; base < cnt; base += U * nth) {
+        C q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * nth, m = idx % Mh, l = idx / Mh;
+            q[u] = C{T(0), T(0)};
+            if (idx < cnt && row0 + l < a.nrows) {
+                const T *xr = x + (row0 + l) * a.x_row;
+                if ((N & 1) == 0) {
+                    q[u] = ldw<COH>(reinterpret_cast<const C *>(xr) + m);
+                } else {
+                    q[u].x = ldw<COH>(xr + 2 * m);
+                    q[u].y = (2 * m + 1 < N) ? ldw<COH>(xr + 2 * m + 1) : T(0);
+                }
             }
         }
-        buf[m * ld + l] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * nth;
+            if (idx < cnt) buf[(idx % Mh) * ld + idx / Mh] = q[u];
+        }
     }
     const int zc = L * (N - Mh);
     for (int idx = tid; idx < zc; idx += nth) buf[(Mh + (idx >> a.lgL)) * ld + (idx & lmask)] = C{T(0), T(0)};
@@ -248,11 +276,20 @@ __device__ __forceinline__ void c2r_tile(const RowsArgs &a, int bx, unsigned cha
     const C *c = reinterpret_cast<const C *>(a.c);
 
     const int cnt = L * np;
-    for (int idx = tid; idx < cnt; idx += nth) {
-        const int k = idx % np, l = idx / np;
-        C v = C{T(0), T(0)};
-        if (row0 + l < a.nrows) v = ldw<COH>(c + ((row0 + l) * a.c_row + k));
-        buf[k * ld + l] = v;
+    constexpr int U = 4;  // loads in flight per thread
+    for (int base = tid; base < cnt; base += U * nth) {
+        C q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * nth, k = idx % np, l = idx / np;
+            q[u] = C{T(0), T(0)};
+            if (idx < cnt && row0 + l < a.nrows) q[u] = ldw<COH>(c + ((row0 + l) * a.c_row + k));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * nth;
+            if (idx < cnt) buf[(idx % np) * ld + idx / np] = q[u];
+        }
     }
     __syncthreads();
 

@@ -42,6 +42,7 @@ import fsp_inputs as I  # noqa: E402
 
 METRIC = "VG free-space solves/s at N=256 (FP32-mix vs FP64, stated err); HBM GB/s; p99 ms"
 FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 rate of a GB300
 PASS_NAMES = ["P1 pad + x-R2C (k_fast_r2c)", "P2 y-FFT (k_fast_col fwd)", "P3 z-FFT * S * z-IFFT (k_fast_col fmi)",
               "P4 y-IFFT (k_fast_col inv)", "P5 x-C2R + crop (k_fast_c2r)"]
 NSRC = 4
@@ -648,6 +649,12 @@ def main():
                    "hbm_gbs_solve": round(sum(pass_bytes(N, 16, 8)) / (t64 * 1e-3) / 1e9, 1),
                    "roofline": roofline(N, 16, 8, f64, "f64", hbm, hbm_kind),
                    "nominal_gflops": round(solve_flops(N) / (t64 * 1e-3) / 1e9, 1),
+                   "roofline_alu": {"bound": "alu", "achieved": round(solve_flops(N) / (t64 * 1e-3) / 1e12, 4),
+                                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": round(solve_flops(N) / (t64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                                    "peak_kind": "nominal GB300 FP64 rate (a probe kernel measured 1.20)",
+                                    "flops": "nominal 5 n log2 n per complex FFT of length n, pruned work counted "
+                                             "as full"},
                    "precompute_ms": round(f64["precompute_ms"], 1), "gpu_launches": 5 * f64["K"]}
     tdf = fdf["tmax_ms"] / fdf["K"]
     out["fp64_df"] = {"value": round(fdf["value"], 2), "unit": "solves/s", "steps": fdf["K"], "ms_per_step": round(tdf, 4),

@@ -12,7 +12,14 @@
 //    kept half (Sec. 2.2 steps 2 and 5, pruned);
 //  * in P3 the multiply by S happens in registers and the inverse transform
 //    runs the forward radix schedule in reverse, so its first stage works on
-//    the very registers the forward's last stage produced (no exchange).
+//    the very registers the forward's last stage produced (no exchange);
+//  * P3 also has an odd-spectrum mode (COL_FMO, the field E = -grad phi:
+//    multiplier -i S_a) and every column pass a runtime-geometry form (RG,
+//    non-cubic boxes: strides, line count and k_y fold from the arguments);
+//  * per (type, pass) compile-time choices: the tile shape (Cfg, ColCfg) and
+//    the memory options (ColOpt: L2-only streamed loads, L1 prefetch of the
+//    spectrum, roots table in shared memory), each kept where it measured
+//    faster on the GB300.
 //
 // Stage s (radix R, Ns = product of the earlier radices) on butterflies
 // b = t + k*TPL (k < V/R) of thread t: inputs at positions b + r n/R,

@@ -139,3 +139,22 @@ def test_aniso_256x256x512_sampled(fsp, orc, dtype):
     print("256x256x512 he %s sampled E_max %.2e" % (dtype, err))
     assert err <= TOL3[dtype]
     p.close()
+
+
+def test_aniso_512x512x1024_weak_scaling_shape(fsp, orc):
+    """The 512^2 x 1024 grid of the paper's weak-scaling runs (Sec. 3.2) on
+    one GPU (n_z = 1024: the generic engine for the z lines of 2048), HE,
+    FP32-mixed, at sampled points against the oracle's direct sum."""
+    n, L = (512, 512, 1024), (1.0, 1.0, 2.0)
+    h = tuple(L[a] / n[a] for a in range(3))
+    rho = I.gaussian_mixture3(n, L).astype(np.float32)
+    p = fsp.Plan(n, L, "he", "f32")
+    phi = p.solve(to_dev(rho, "f32")).cpu().numpy().ravel()
+    p.close()
+    rng = np.random.default_rng(5121024)
+    tot = n[0] * n[1] * n[2]
+    pts = np.concatenate([rng.integers(0, tot, 4), [tot // 2 + n[0] * n[1] // 2 + n[0] // 2]])
+    ref = orc.solve_direct3(orc.kernel_T3("he", n, h), rho.astype(np.float64), h, pts)
+    err = float(np.max(np.abs(phi[pts] - ref)) / np.max(np.abs(ref)))
+    print("512x512x1024 he f32 sampled E_max %.2e" % err)
+    assert err <= TOL["f32"]

@@ -107,7 +107,8 @@ fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo a
  *
  * A cube (nx = ny = nz, hx = hy = hz) returns the cubic plan of
  * fsp_plan_create, with its specialised kernels.  Otherwise, when every n_a
- * is a power of two in [32, 512], the solve runs on the specialised kernels
+ * is a power of two in [32, 512] (FSP_F32_MIXED: n_y and n_z up to 1024), the
+ * solve runs on the specialised kernels
  * (rows of n_x; column passes with runtime strides), in any dtype; else on
  * the generic engine (any 2/3/5-smooth 2 n_a, and 4 n_a for FSP_VG), dtype
  * FSP_F64 or FSP_F32_MIXED (FSP_F64_DF: FSP_EUNSUPPORTED).  FSP_VG and

@@ -935,11 +935,14 @@ fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double 
     {
         const char *g = std::getenv("FSP_GENERIC_ONLY");
         const bool generic_only = g && g[0] == '1';
-        fast_ok = true;
-        for (int a = 0; a < 3; ++a)
-            fast_ok = fast_ok && (dtype == FSP_F64      ? fast::has<double>(nn[a])
-                                  : dtype == FSP_F64_DF ? fast::has<df>(nn[a])
-                                                        : fast::has<float>(nn[a]));
+        // rows of n_x; column passes of 2 n_y and 2 n_z
+        fast_ok = dtype == FSP_F64 ? fast::has<double>(nx) && fast::has_col_rg<double>(2 * ny) &&
+                                         fast::has_col_rg<double>(2 * nz)
+                  : dtype == FSP_F64_DF ? fast::has<df>(nx) && fast::has_col_rg<df>(2 * ny) &&
+                                              fast::has_col_rg<df>(2 * nz)
+                                        : fast::has<float>(nx) && fast::has_col_rg<float>(2 * ny) &&
+                                              fast::has_col_rg<float>(2 * nz);
+        fast_ok = fast_ok && ny >= 32 && nz >= 32;
         if (dtype != FSP_F64_DF) fast_ok = fast_ok && !generic_only;
     }
     if (dtype == FSP_F64_DF && !fast_ok) return FSP_EUNSUPPORTED;  // double-float: specialised kernels only

@@ -652,6 +652,7 @@ FSP_CFG(float, 128, 16, 16, 8, 16, 1)
 FSP_CFG(float, 256, 16, 16, 16, 16, 1)
 FSP_CFG(float, 512, 32, 16, 16, 32, 1)
 FSP_CFG(float, 1024, 16, 16, 16, 16, 4)
+FSP_CFG(float, 2048, 16, 8, 16, 16, 8)  // column passes of non-cubic boxes only (an axis of 1024)
 FSP_CFG(double, 32, 8, 16, 4, 8, 1)
 FSP_CFG(double, 64, 8, 16, 8, 8, 1)
 FSP_CFG(double, 128, 16, 8, 8, 16, 1)
@@ -740,6 +741,7 @@ template <typename T, int MODE> cudaError_t launch_col_rg(int n, const ColArgs &
     case 256: return launch_col_rg_n<T, 256, MODE>(a, nbatch, s);
     case 512: return launch_col_rg_n<T, 512, MODE>(a, nbatch, s);
     case 1024: return launch_col_rg_n<T, 1024, MODE>(a, nbatch, s);
+    case 2048: return launch_col_rg_n<T, 2048, MODE>(a, nbatch, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -798,6 +800,17 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
 // the column passes of non-cubic boxes (runtime geometry), in translation
 // units of their own
 #define FSP_FAST_RG_INSTANTIATE(T)                                                                             \
+    template <> bool has_col_rg<T>(int n) {                                                                    \
+        switch (n) {                                                                                           \
+        case 64: return Cfg<T, 64>::Ok;                                                                        \
+        case 128: return Cfg<T, 128>::Ok;                                                                      \
+        case 256: return Cfg<T, 256>::Ok;                                                                      \
+        case 512: return Cfg<T, 512>::Ok;                                                                      \
+        case 1024: return Cfg<T, 1024>::Ok;                                                                    \
+        case 2048: return Cfg<T, 2048>::Ok;                                                                    \
+        }                                                                                                      \
+        return false;                                                                                          \
+    }                                                                                                          \
     template <> cudaError_t col_rg<T>(int mode, int n, const ColArgs &a, int nb, cudaStream_t s) {              \
         switch (mode) {                                                                                        \
         case COL_FWD: return launch_col_rg<T, COL_FWD>(n, a, nb, s);                                           \

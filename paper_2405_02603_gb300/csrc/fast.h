@@ -50,6 +50,8 @@ template <typename T> cudaError_t p5(int N, const RowArgs &a, cudaStream_t s);
 // A column pass (mode COL_FWD, COL_INV or COL_FMI) of length n on a non-cubic
 // box: strides from `a`, lines k_x <= a.nlines - 1, P3's k_y fold at a.half_b
 template <typename T> cudaError_t col_rg(int mode, int n, const ColArgs &a, int nbatch, cudaStream_t s);
+// true when col_rg has a shape for lines of length n (64 .. 1024; FP32 also 2048)
+template <typename T> bool has_col_rg(int n);
 // P3 of a field component: z-FFT * (-i S_a, odd in the axis a.odd) * z-IFFT
 template <typename T> cudaError_t p3_odd(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 

@@ -63,6 +63,23 @@ def test_aniso_fast_path(fsp, orc, n, L, algo, dtype):
     p.close()
 
 
+@pytest.mark.parametrize("algo", ["he", "vg_dct"])
+def test_aniso_fast_z_lines_of_2048(fsp, orc, algo):
+    """An axis of 1024 cells: FP32 column passes of length 2048 (the shape the
+    512^2 x 1024 grid needs), whole field against the oracle; FP64 has no
+    such shape and takes the generic engine."""
+    n, L = (32, 32, 1024), (0.7, 0.7, 1.4)
+    h = _h(n, L)
+    rho = I.gaussian_mixture3(n, L, seed=1024).astype(np.float32).astype(np.float64)
+    p = fsp.Plan(n, L, algo, "f32")
+    assert p.fast_path
+    phi = p.solve(to_dev(rho, "f32")).cpu().numpy()
+    p.close()
+    ref = orc.solve_fft3(orc.kernel_T3(algo, n, h), rho, h)
+    assert e_max(phi, ref) <= TOL3["f32"]
+    assert not fsp.Plan(n, L, algo, "f64").fast_path
+
+
 def test_aniso_fast_equals_generic(fsp, monkeypatch):
     n, L = (64, 32, 128), (1.0, 1.0, 1.5)
     rho = to_dev(I.gaussian_mixture3(n, L, seed=5), "f64")
@@ -143,12 +160,13 @@ def test_aniso_256x256x512_sampled(fsp, orc, dtype):
 
 def test_aniso_512x512x1024_weak_scaling_shape(fsp, orc):
     """The 512^2 x 1024 grid of the paper's weak-scaling runs (Sec. 3.2) on
-    one GPU (n_z = 1024: the generic engine for the z lines of 2048), HE,
-    FP32-mixed, at sampled points against the oracle's direct sum."""
+    one GPU (the specialised kernels; z lines of 2048), HE, FP32-mixed, at
+    sampled points against the oracle's direct sum."""
     n, L = (512, 512, 1024), (1.0, 1.0, 2.0)
     h = tuple(L[a] / n[a] for a in range(3))
     rho = I.gaussian_mixture3(n, L).astype(np.float32)
     p = fsp.Plan(n, L, "he", "f32")
+    assert p.fast_path
     phi = p.solve(to_dev(rho, "f32")).cpu().numpy().ravel()
     p.close()
     rng = np.random.default_rng(5121024)

@@ -64,8 +64,9 @@ typedef enum { FSP_HE = 0, FSP_VG = 1, FSP_VG_DCT = 2 } fsp_algo;
  * relative), but the transforms run in double-float arithmetic (each value a
  * pair of floats, hi + lo) on the FP32 pipes, which on this GPU are far faster
  * than its FP64 pipes; the spectrum is the FP64 one split into float pairs.
- * Only for N = 32, 64, 128, 256, 512 (FSP_EUNSUPPORTED otherwise); not in
- * batches. */
+ * Only where the specialised kernels run: N = 32, 64, 128, 256, 512, or a
+ * non-cubic box whose sizes are powers of two in that range
+ * (FSP_EUNSUPPORTED otherwise); not in batches. */
 typedef enum { FSP_F64 = 0, FSP_F32_MIXED = 1, FSP_F64_DF = 2 } fsp_dtype;
 
 typedef struct fsp_plan fsp_plan;
@@ -82,7 +83,7 @@ const char *fsp_status_str(fsp_status s);
  * L      cube side, L > 0 and finite.
  * h      grid spacing; must equal L/N to 1e-12 relative (else FSP_EINVAL).
  * algo   FSP_HE, FSP_VG or FSP_VG_DCT.
- * dtype  FSP_F64 or FSP_F32_MIXED.
+ * dtype  FSP_F64, FSP_F32_MIXED or FSP_F64_DF.
  * stream the precompute (plan-time Green's spectrum, Sec. 2.2 step 3, Sec. 2.3
  *        and Sec. 2.4) runs on this stream; the call returns after it has
  *        completed (it synchronises the stream) and temporaries are freed.
@@ -225,8 +226,9 @@ fsp_status fsp_plan_destroy(fsp_plan *plan);
 fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents);
 
 /* 1 when this plan's solves run the specialised power-of-two kernels (N = 32,
- * 64, 128, 256, 512; compile-time radix schedules, register-resident), 0 when
- * they run the generic mixed-radix engine, -1 for an invalid plan.  Setting
+ * 64, 128, 256, 512, or a non-cubic box of such sizes; compile-time radix
+ * schedules, register-resident), 0 when they run the generic mixed-radix
+ * engine, -1 for an invalid plan.  Setting
  * the environment variable FSP_GENERIC_ONLY=1 before fsp_plan_create forces
  * the generic engine (used to test both paths on the same sizes). */
 int fsp_plan_uses_fast_path(const fsp_plan *plan);

@@ -1,0 +1,25 @@
+"""The committed ncu summaries: each gives the full command that made it,
+the command runs committed files only (bench.py, the package), and every ncu
+command leaves the GPU clocks alone (--clock-control none).  No GPU."""
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _commands(text):
+    return [c for c in re.findall(r"`([^`]*ncu [^`]*)`", text)]
+
+
+def test_every_summary_has_a_committed_command():
+    files = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+    assert files
+    for path in files:
+        cmds = _commands(open(path).read())
+        assert cmds, path
+        for c in cmds:
+            assert "--clock-control none" in c, (path, c)
+            assert "_work" not in c and "/root/" not in c, (path, c)
+            for script in re.findall(r"python\s+(\S+\.py)", c):
+                assert os.path.exists(os.path.join(ROOT, script)), (path, script)

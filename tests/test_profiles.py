@@ -9,7 +9,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _commands(text):
-    return [c for c in re.findall(r"`([^`]*ncu [^`]*)`", text)]
+    """The inline code spans (odd segments between backticks) that run ncu."""
+    spans = text.split("`")[1::2]
+    return [c for c in spans if re.search(r"(^|\s)ncu\s+-", c)]
 
 
 def test_every_summary_has_a_committed_command():

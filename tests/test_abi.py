@@ -29,6 +29,22 @@ def test_every_declared_symbol_is_exported(L):
         assert hasattr(L, s), s
 
 
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    """include/fsp.h is a plain C interface: it compiles as C11 (pedantic)
+    and as C++17 without CUDA headers."""
+    import shutil
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text('#include "fsp.h"\nint main(void) { fsp_plan *p = 0; (void)p; return (int)FSP_OK; }\n')
+    inc = os.path.join(ROOT, "include")
+    if shutil.which("gcc"):
+        subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I", inc,
+                        str(src)], check=True)
+    if shutil.which("g++"):
+        subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, "-x", "c++", str(src)],
+                       check=True)
+
+
 def test_status_strings(L):
     for code in range(7):
         assert L.fsp_status_str(code).startswith(b"FSP_")

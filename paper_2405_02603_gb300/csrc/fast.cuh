@@ -316,13 +316,16 @@ template <int n, int MODE> struct ColGeo {
 //   PF:  prefetch the thread's spectrum values into L1 before the forward
 //        transform (P3: their latency overlaps the transform; FP32 P3 -5 %).
 //   TWS: roots table in shared memory: double-float P3 -11 % and P2 -2 %,
-//        the FP32 field P3 (COL_FMO) faster too; FP32 P3 of the potential
-//        (COL_FMI), native FP64 and every P4 are slower or unchanged with it.
-template <typename T, int MODE> struct ColOpt {
+//        the FP32 field P3 (COL_FMO) and the FP32 P3 on lines of 1024 (-4 %)
+//        faster too; the FP32 P3 of the potential on lines of 512, native
+//        FP64 and every P4 are slower or unchanged with it.
+template <typename T, int MODE, int n> struct ColOpt {
     static constexpr bool ZL = MODE == COL_FMI || MODE == COL_FMO;
     static constexpr bool DF = std::is_same<T, df>::value;
+    static constexpr bool F32 = std::is_same<T, float>::value;
     static constexpr bool PF = ZL && !DF;
-    static constexpr bool TWS = (DF && MODE != COL_INV) || (MODE == COL_FMO && !std::is_same<T, double>::value);
+    static constexpr bool TWS = (DF && MODE != COL_INV) || (MODE == COL_FMO && !std::is_same<T, double>::value) ||
+                                (MODE == COL_FMI && F32 && n == 1024);
 };
 
 // RG (a non-cubic box): the strides, the number of lines (k_x <= n_x) and the
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         }
     }
     constexpr bool ok = true;
-    using O = ColOpt<T, MODE>;
+    using O = ColOpt<T, MODE, n>;
     const C *tw = reinterpret_cast<const C *>(a.tw);
     if constexpr (O::TWS) {
         // the roots table in shared memory after the exchange buffer (first
@@ -699,7 +702,7 @@ template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a
         return cudaErrorInvalidValue;
     } else {
         auto kern = k_fast_col<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE>;
-        const size_t sm = sizeof(cx_t<T>) * n * (K::L + 1) + (ColOpt<T, MODE>::TWS ? sizeof(cx_t<T>) * n : 0);
+        const size_t sm = sizeof(cx_t<T>) * n * (K::L + 1) + (ColOpt<T, MODE, n>::TWS ? sizeof(cx_t<T>) * n : 0);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         // N/L full tiles per batch row, plus nbatch/N block rows of Nyquist tiles
@@ -725,7 +728,7 @@ template <typename T, int n, int MODE> cudaError_t launch_col_rg_n(const ColArgs
         ColArgs b = a;
         b.nbatch = nbatch;
         b.xrows = (nbatch / K::L + nx / K::L - 1) / (nx / K::L);
-        const size_t sm = sizeof(cx_t<T>) * n * (K::L + 1) + (ColOpt<T, MODE>::TWS ? sizeof(cx_t<T>) * n : 0);
+        const size_t sm = sizeof(cx_t<T>) * n * (K::L + 1) + (ColOpt<T, MODE, n>::TWS ? sizeof(cx_t<T>) * n : 0);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)(nx / K::L), (unsigned)(nbatch + b.xrows));

@@ -47,6 +47,10 @@ MUTANTS = [
     ("direct_sum_h3", "out[p] = h * h * h * (sum + comp);", "out[p] = h * h * (sum + comp);"),
     ("padding_bound", "for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 0; x < N; ++x) r2[",
      "for (int z = 0; z < N; ++z)\n        for (int y = 0; y < N; ++y)\n            for (int x = 1; x < N; ++x) r2["),
+    ("spectrum_scale", "S[((size_t)z * k1 + y) * k1 + x] = creal(g2[((size_t)z * n2 + y) * n2 + x]) * scale;",
+     "S[((size_t)z * k1 + y) * k1 + x] = creal(g2[((size_t)z * n2 + y) * n2 + x]) * scale * 8.0;"),
+    ("spectrum_index", "S[((size_t)z * k1 + y) * k1 + x] = creal(g2[((size_t)z * n2 + y) * n2 + x]) * scale;",
+     "S[((size_t)z * k1 + y) * k1 + x] = creal(g2[((size_t)y * n2 + z) * n2 + x]) * scale;"),
 ]
 
 # planted mistakes in the field functions (caught by _field_pins)
@@ -111,6 +115,9 @@ def _pins(orc):
     e_vg = A.rel_l2(orc.solve("vg", I.gaussian(16)), A.gaussian_potential(16))
     res["gauss_vg16"] = 1e-4 <= e_vg <= 1e-2
     res["vg_far_field"] = _far_field_err(orc, "vg_dct", 16) < 1e-2
+    Ts = np.random.default_rng(7).standard_normal((6, 6, 6))  # no symmetry between its axes
+    res["spectrum_vs_dctn"] = np.allclose(orc.spectrum(Ts, 0.2), scipy.fft.dctn(Ts, type=1) * 0.2 ** 3 / 10 ** 3,
+                                          rtol=0, atol=1e-12 * np.abs(Ts).max())
     return res
 
 
@@ -193,6 +200,8 @@ ANISO_MUTANTS = [
     ("he_field3_spacing", "double r[3] = {x * h[0], y * h[1], z * h[2]};", "double r[3] = {x * h[0], y * h[0], z * h[2]};"),
     ("field_doubled3_odd_axis", "odd_sign(m[a], n[a]) * F[((size_t)fold2(z, n[2])", "odd_sign(m[a], n[0]) * F[((size_t)fold2(z, n[2])"),
     ("vg_field3_ka_axis", "double ka = j[a] == -2 * n[a] ? 0.0 : dk[a] * j[a];", "double ka = j[a] == -2 * n[a] ? 0.0 : dk[0] * j[a];"),
+    ("spectrum3_scale", "S[((size_t)z * k[1] + y) * k[0] + x] = creal(g2[((size_t)z * d[1] + y) * d[0] + x]) * scale;",
+     "S[((size_t)z * k[1] + y) * k[0] + x] = creal(g2[((size_t)z * d[1] + y) * d[0] + x]) * scale * 2.0;"),
     ("vgdct3_scale_axis", "double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[1] * h[1]) * (4.0 * n[2] * h[2]));",
      "double scale = 1.0 / ((4.0 * n[0] * h[0]) * (4.0 * n[0] * h[1]) * (4.0 * n[2] * h[2]));"),
 ]
@@ -240,6 +249,11 @@ def _aniso_pins(orc):
     xx = I.cell_centres(nf[0], Lf[0])[None, None, :] - c[0]
     far = np.sqrt(xx * xx + yy * yy + zz * zz) > 1.2
     res["far_field"] = float(np.max(np.abs(phi[far] - ex[far]) / ex[far])) < 1e-2
+    import scipy.fft as sfft
+    T3 = orc.kernel_T3("vg_dct", n, h)
+    res["spectrum3_vs_dctn"] = np.allclose(orc.spectrum3(T3, h),
+                                           sfft.dctn(T3, type=1) * h[0] * h[1] * h[2] / (8.0 * n[0] * n[1] * n[2]),
+                                           rtol=0, atol=1e-12 * np.abs(T3).max() * h[0] * h[1] * h[2])
     # the field on a non-cubic box
     nf3, hf3 = (6, 4, 5), (0.2, 0.3, 0.25)
     rr = I.random_field3(nf3, 6)

@@ -386,9 +386,12 @@ fsp_status fsp_tuning_set(const char *text);
  *
  * Scratch: the two transform buffers and the roots tables live in one
  * file-scope device array of 2.36 MB (N = 32 at row pitch 48), which every
- * GPU that loads the library holds until the process exits.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress) and
- * keeps it; make that first call before any stream capture.  All calls on a
+ * GPU that loads the library holds until the process exits.  Every call looks
+ * up that array's device address in the current context
+ * (cudaGetSymbolAddress, which allocates nothing), so the address stays right
+ * after a device reset or a new primary context.  The first lookup in a
+ * context may load the library's device code: make the first call on a device
+ * before any stream capture.  All calls on a
  * device share the one array and leave their intermediate values in it; no
  * part of it needs to start at zero (each call writes every element before
  * reading it).  Calls whose device work overlaps in time (different streams,

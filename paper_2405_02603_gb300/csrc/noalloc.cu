@@ -18,11 +18,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <cstring>
-#include <mutex>
 
 #include "../../include/fsp.h"
 #include "kernels.cuh"
+#include "tiles.h"
 
 using namespace fsp;
 
@@ -32,7 +31,6 @@ constexpr int kNoAllocMaxN = 32;
 constexpr int kNoAllocPitch = 48;  // N+1 rounded up to 16, for N = 32
 constexpr size_t kNoAllocW1 = (size_t)kNoAllocMaxN * kNoAllocMaxN * kNoAllocPitch;
 constexpr size_t kNoAllocComplex = 3 * kNoAllocW1 + 3 * kNoAllocMaxN;
-constexpr int kMaxDevices = 64;
 
 }  // namespace
 
@@ -41,59 +39,26 @@ static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocComplex];
 
 namespace {
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices] = {};
-
-bool smooth235(long long n) {
-    if (n < 1) return false;
-    for (int p : {2, 3, 5})
-        while (n % p == 0) n /= p;
-    return n == 1;
+// The plan-based solve's radix schedule and tile rule (tiles.h).
+bool noalloc_cfg(int n, int positions, int want_lgL, TileCfg &c) {
+    return make_cfg(n, positions, sizeof(double2), want_lgL, c);
 }
 
-// Same radix schedule and tile rule as the plan-based solve.
-bool noalloc_cfg(int n, int positions, int want_lgL, Stages &st, int &tpl, int &lgL) {
-    std::memset(&st, 0, sizeof(st));
-    st.n = n;
-    int m = n;
-    while (m % 5 == 0) m /= 5, ++st.n5;
-    while (m % 3 == 0) m /= 3, ++st.n3;
-    while (m % 8 == 0) m /= 8, ++st.n8;
-    if (m % 4 == 0) m /= 4, st.last = 4;
-    else if (m % 2 == 0) m /= 2, st.last = 2;
-    if (m != 1) return false;
-    const int radices[4] = {st.n5 ? 5 : 0, st.n3 ? 3 : 0, st.n8 ? 8 : 0, st.last};
-    for (tpl = n / 16 < 1 ? 1 : n / 16;; ++tpl) {
-        bool ok = true;
-        for (int R : radices)
-            if (R && (n / R + tpl - 1) / tpl > kMaxV / R) ok = false;
-        if (ok) break;
-    }
-    for (lgL = want_lgL; lgL >= 0; --lgL) {
-        const int L = 1 << lgL;
-        if (L * tpl <= 512 && (size_t)positions * (L + 1) * sizeof(double2) <= 200 * 1024) return true;
-    }
-    return false;
-}
-
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in and must never be
-// passed to a kernel).
+// Device address of the scratch array in the current device's context.  The
+// host-side symbol is only a stand-in and must never be passed to a kernel.
+// The address is looked up on every call and never cached: after a device
+// reset, or when the primary context is torn down and created again, the
+// module is loaded anew and the array may sit at another address.  The lookup
+// allocates nothing and is not a stream operation; the first one in a context
+// may load this library's device code.
 fsp_status noalloc_scratch(double2 **out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return FSP_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return FSP_ECUDA;
-        }
-        g_noalloc_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return FSP_ECUDA;
     }
-    *out = reinterpret_cast<double2 *>(g_noalloc_addr[dev]);
+    *out = reinterpret_cast<double2 *>(p);
     return FSP_OK;
 }
 
@@ -101,14 +66,12 @@ fsp_status noalloc_scratch(double2 **out) {
 
 extern "C" fsp_status fsp_solve_noalloc(int N, const double *S, const double *rho, double *phi, fsp_stream stream) {
     if (N < 2) return FSP_EINVAL;
-    if (N > kNoAllocMaxN || !smooth235(2LL * N)) return FSP_EUNSUPPORTED;
+    if (N > kNoAllocMaxN || !is_235_smooth(2LL * N)) return FSP_EUNSUPPORTED;
     if (!S || !rho || !phi) return FSP_EINVAL;
     for (const void *q : {(const void *)S, (const void *)rho, (const void *)phi})
         if (reinterpret_cast<uintptr_t>(q) & 15u) return FSP_EINVAL;
-    Stages st_row, st_col;
-    int tpl_row, lgL_row, tpl_col, lgL_col;
-    if (!noalloc_cfg(N, N + 1, 3, st_row, tpl_row, lgL_row) || !noalloc_cfg(2 * N, 2 * N, 3, st_col, tpl_col, lgL_col))
-        return FSP_EUNSUPPORTED;
+    TileCfg row, col;
+    if (!noalloc_cfg(N, N + 1, 3, row) || !noalloc_cfg(2 * N, 2 * N, 3, col)) return FSP_EUNSUPPORTED;
     double2 *base = nullptr;
     fsp_status status = noalloc_scratch(&base);
     if (status != FSP_OK) return status;
@@ -124,11 +87,11 @@ extern "C" fsp_status fsp_solve_noalloc(int N, const double *S, const double *rh
     // P1: pad + x-R2C
     RowsArgs r{};
     r.x = rho, r.c = W1, r.x_row = N, r.c_row = P, r.N = N, r.nrows = N * N;
-    r.lgL = lgL_row, r.tpl = tpl_row, r.st = st_row, r.tw = tw_n, r.tw2 = tw_2n;
+    r.lgL = row.lgL, r.tpl = row.tpl, r.st = row.st, r.tw = tw_n, r.tw2 = tw_2n;
     if ((e = launch_r2c_rows<double>(r, s)) != cudaSuccess) return FSP_ECUDA;
     // P2: y-FFT
     LinesArgs a{};
-    a.st = st_col, a.tpl = tpl_col, a.lgL = lgL_col, a.tw = tw_2n;
+    a.st = col.st, a.tpl = col.tpl, a.lgL = col.lgL, a.tw = tw_2n;
     a.in = W1, a.out = W2;
     a.in_pos = P, a.in_line = 1, a.in_batch = (long long)N * P;
     a.out_pos = P, a.out_line = 1, a.out_batch = 2LL * N * P;

@@ -35,6 +35,30 @@ def test_noalloc_matches_plan_solve_twice(fsp, algo, N):
     plan.close()
 
 
+@pytest.mark.parametrize("algo", ["he", "vg"])
+@pytest.mark.parametrize("N", [6, 16, 32])
+def test_noalloc_on_oracle_spectrum_matches_oracle_solve(fsp, orc, algo, N):
+    """The spectrum and the expected result both come from the CPU oracle:
+    nothing the GPU computed enters the comparison but the solve itself."""
+    import torch
+    L, h = 1.0, 1.0 / N
+    T = orc.kernel_T(algo, N, L)
+    S = torch.from_numpy(np.ascontiguousarray(orc.spectrum(T, h))).cuda()
+    lib = fsp.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call, rho_np in enumerate((I.gaussian_mixture(N), I.random_field(N, seed=7))):
+        ref = orc.solve_fft(T, rho_np, h)
+        rho = torch.from_numpy(rho_np).cuda()
+        phi = torch.full_like(rho, float("nan"))
+        st = lib.fsp_solve_noalloc(N, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+                                   ctypes.c_void_p(phi.data_ptr()), stream)
+        assert st == fsp.FSP_OK
+        torch.cuda.synchronize()
+        got = phi.cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= 1e-12, (N, algo, call, err)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(fsp):
     import torch
     L = fsp.lib()

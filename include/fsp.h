@@ -206,8 +206,22 @@ fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void
                                fsp_stream stream);
 
 /* Wait for all work enqueued for this plan's solves and report any
- * asynchronous CUDA error as FSP_ECUDA. */
+ * asynchronous CUDA error as FSP_ECUDA.  FSP_ETIMEOUT: a bounded device-side
+ * wait of a solve since the last check ran out (the results of that solve are
+ * not valid; the plan and the context stay usable; the flag is cleared). */
 fsp_status fsp_plan_sync(fsp_plan *plan, fsp_stream stream);
+
+/* Time limit (milliseconds, > 0; default 1000) of each device-side wait in
+ * this plan's solves.  Only the TMA-staged P3 waits (FP32-mixed, N = 64, 128,
+ * 256, selected by FSP_P3_TMA=1 in the environment at plan creation; the
+ * default register-direct P3 measured faster): on an mbarrier, for each input
+ * tile of Sec. 2.2 step 4's z-transforms. */
+fsp_status fsp_plan_set_wait_timeout(fsp_plan *plan, double ms);
+/* Fault injection for tests, made on the host: the next solve's TMA-staged P3
+ * expects 16 bytes more per input tile than the copy delivers, so each of its
+ * CTAs' first wait can only end by the time limit; fsp_plan_sync then returns
+ * FSP_ETIMEOUT.  FSP_EUNSUPPORTED when the plan's P3 has no such wait. */
+fsp_status fsp_plan_inject_stall(fsp_plan *plan);
 
 /* Release the plan and all its device memory.  Waits for the device first.
  * A destroyed or unknown pointer returns FSP_EINVAL (plans are tracked in a

@@ -79,6 +79,8 @@ def lib(build_if_missing=True):
     L.fsp_solve_field.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fsp_plan_uses_fast_path.argtypes = [vp]
     L.fsp_plan_uses_fast_path.restype = i
+    L.fsp_plan_set_wait_timeout.argtypes = [vp, d]
+    L.fsp_plan_inject_stall.argtypes = [vp]
     vpp = ctypes.POINTER(vp)
     L.fsp_batch_create.argtypes = [vpp, vpp, vpp, vpp, i, vp]
     L.fsp_batch_launch.argtypes = [vp, vp]
@@ -108,7 +110,7 @@ def lib(build_if_missing=True):
         getattr(L, name).restype = i
     for name in ("fsp_plan_set_timing", "fsp_plan_create", "fsp_plan_create_aniso", "fsp_solve", "fsp_solve_host", "fsp_plan_sync", "fsp_plan_destroy",
                  "fsp_plan_spectrum", "fsp_kernel_T", "fsp_fft_c2c", "fsp_solve_noalloc", "fsp_plan_field_init",
-                 "fsp_solve_field"):
+                 "fsp_solve_field", "fsp_plan_set_wait_timeout", "fsp_plan_inject_stall"):
         getattr(L, name).restype = i
     _lib = L
     table = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.txt")

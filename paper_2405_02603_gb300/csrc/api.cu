@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <atomic>
 #include <condition_variable>
 #include <deque>
 #include <cmath>
@@ -17,6 +18,7 @@
 #include <thread>
 #include <unordered_map>
 #include <tuple>
+#include <type_traits>
 #include <unordered_set>
 #include <vector>
 
@@ -373,6 +375,10 @@ struct fsp_plan {
     cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
     TileCfg row, col;
     bool fast = false;  // specialised power-of-two kernels (fast.cuh) serve this N
+    bool p3_tma = false;  // P3 by the TMA-staged persistent kernel (p3_tma.cuh)
+    unsigned *err = nullptr;  // device word: bit 0 = a bounded device-side wait timed out
+    unsigned long long wait_timeout_ns = 1000000000ull;  // per device-side wait
+    mutable std::atomic<unsigned> inject_tx{0};  // fault injection, consumed by the next solve
     // field solves (fsp_plan_field_init): the spectra of F_x, F_y, F_z and the
     // third workspace the out-of-place P3 of each component writes
     void *SF[3] = {}, *W3 = nullptr;
@@ -404,7 +410,8 @@ size_t plan_points(const fsp_plan *p) {
 
 void plan_free(fsp_plan *p) {
     for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi, p->pipe_rho[0], p->pipe_rho[1],
-                    p->pipe_phi[0], p->pipe_phi[1], p->SF[0], p->SF[1], p->SF[2], p->W3, p->tw_y, p->tw_z})
+                    p->pipe_phi[0], p->pipe_phi[1], p->SF[0], p->SF[1], p->SF[2], p->W3, p->tw_y, p->tw_z,
+                    (void *)p->err})
         if (q) cudaFree(q);
     for (cudaStream_t q : {p->pipe_h2d, p->pipe_d2h})
         if (q) cudaStreamDestroy(q);
@@ -435,7 +442,17 @@ cudaError_t enqueue_solve_fast(const fsp_plan *p, const void *rho, void *phi, vo
     a.in = a.out = W2;  // P3: z-FFT * S * z-IFFT, in place, batch ky
     a.in_pos = a.out_pos = 2LL * N * P, a.in_batch = a.out_batch = P;
     a.S = p->S, a.s_pos = (long long)(N + 1) * P, a.s_batch = P, a.half = N;
-    if ((e = fast::p3<T>(N, a, 2 * N, s)) != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+        if (p->p3_tma) {
+            fast::P3Wait w{p->err, p->wait_timeout_ns, p->inject_tx.exchange(0)};
+            e = fast::p3_tma<float>(N, W2, p->S, p->tw_2n, w, s);
+        }
+        else
+            e = fast::p3<T>(N, a, 2 * N, s);
+    } else {
+        e = fast::p3<T>(N, a, 2 * N, s);
+    }
+    if (e != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
     a.in = W2, a.out = W1;  // P4: y-IFFT, W2 -> W1 (y < N)
     a.in_pos = P, a.in_batch = 2LL * N * P, a.out_pos = P, a.out_batch = (long long)N * P;
@@ -793,6 +810,10 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
         const bool generic_only = g && g[0] == '1';
         p->fast = dtype == FSP_F64_DF ||
                   (!generic_only && (dtype == FSP_F64 ? fast::has<double>(N) : fast::has<float>(N)));
+        // the TMA-staged P3 only with FSP_P3_TMA=1: measured slower than the
+        // register-direct P3 on the GB300 (kept for the A/B and its tests)
+        const char *t = std::getenv("FSP_P3_TMA");
+        p->p3_tma = p->fast && dtype == FSP_F32_MIXED && fast::has_p3_tma<float>(N) && t && t[0] == '1';
     }
     auto fail = [&](fsp_status e) {
         cudaStreamSynchronize(s);
@@ -802,7 +823,10 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     const size_t k1 = N + 1;
     const size_t sbytes = k1 * k1 * p->P * p->rsize;
     const size_t w1 = (size_t)N * N * p->P * csize, w2 = 2 * w1;
-    DevBuf bS, bW1, bW2, bt1, bt2;
+    DevBuf bS, bW1, bW2, bt1, bt2, berr;
+    if ((st = alloc_or_nomem(berr, 16)) != FSP_OK) return fail(st);
+    p->err = static_cast<unsigned *>(berr.release());
+    if (cudaMemsetAsync(p->err, 0, 16, s) != cudaSuccess) return fail(FSP_ECUDA);
     if ((st = alloc_or_nomem(bS, sbytes)) != FSP_OK) return fail(st);
     if (with_workspace && (st = alloc_or_nomem(bW1, w1)) != FSP_OK) return fail(st);
     if (with_workspace && (st = alloc_or_nomem(bW2, w2)) != FSP_OK) return fail(st);
@@ -1147,7 +1171,18 @@ fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void
 
 fsp_status fsp_plan_sync(fsp_plan *plan, fsp_stream stream) {
     if (!plan_live(plan)) return FSP_EINVAL;
-    return cuda_status(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FSP_ECUDA;
+    if (!plan->err) return FSP_OK;
+    // a bounded device-side wait that expired since the last check
+    unsigned flags = 0;
+    if (cudaMemcpyAsync(&flags, plan->err, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FSP_ECUDA;
+    if (flags == 0) return FSP_OK;
+    if (cudaMemsetAsync(plan->err, 0, sizeof(flags), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return FSP_ECUDA;
+    return FSP_ETIMEOUT;
 }
 
 fsp_status fsp_plan_destroy(fsp_plan *plan) {
@@ -1172,6 +1207,19 @@ fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents)
         if (!events[i]) return FSP_EINVAL;
     for (int i = 0; i < 6; ++i) plan->ev[i] = reinterpret_cast<cudaEvent_t>(events[i]);
     plan->timing = true;
+    return FSP_OK;
+}
+
+fsp_status fsp_plan_set_wait_timeout(fsp_plan *plan, double ms) {
+    if (!plan_live(plan) || !(ms > 0.0) || !(ms < 1e9)) return FSP_EINVAL;
+    plan->wait_timeout_ns = (unsigned long long)(ms * 1e6);
+    return FSP_OK;
+}
+
+fsp_status fsp_plan_inject_stall(fsp_plan *plan) {
+    if (!plan_live(plan)) return FSP_EINVAL;
+    if (!plan->p3_tma) return FSP_EUNSUPPORTED;
+    plan->inject_tx.store(16);
     return FSP_OK;
 }
 

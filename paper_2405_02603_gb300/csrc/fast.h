@@ -54,6 +54,17 @@ template <typename T> cudaError_t col_rg(int mode, int n, const ColArgs &a, int 
 template <typename T> bool has_col_rg(int n);
 // P3 of a field component: z-FFT * (-i S_a, odd in the axis a.odd) * z-IFFT
 template <typename T> cudaError_t p3_odd(int N, const ColArgs &a, int nbatch, cudaStream_t s);
+// P3 as a persistent kernel with TMA-staged input tiles (p3_tma.cuh), in
+// place on W2 of the cubic layout.  Each wait for a tile is bounded by
+// timeout_ns; on expiry bit 0 of *err is set.  extra_tx > 0 (fault injection)
+// makes every wait expire.
+struct P3Wait {
+    unsigned *err;
+    unsigned long long timeout_ns;
+    unsigned extra_tx;
+};
+template <typename T> bool has_p3_tma(int N);
+template <typename T> cudaError_t p3_tma(int N, void *w2, const void *S, const void *tw, const P3Wait &w, cudaStream_t s);
 
 }  // namespace fast
 }  // namespace fsp

@@ -615,6 +615,7 @@ def main():
         leg = time_leg(fsp, plan, srcs, dsts, k, W, world, sampler)
         leg["K"] = k
         leg["precompute_ms"] = plan.precompute_ms
+        leg["launches"] = plan.launches
         leg["plan_bytes"] = plan.bytes
         leg["phi0"] = dsts[0].double().cpu().numpy() if rank == 0 else None
         leg["e2e"] = e2e_leg(fsp, plan, host[0], dtype, max(20, k // 10), 3) if dtype == "f32" else None
@@ -640,7 +641,7 @@ def main():
            "hbm_gbs_solve": round(sum(pass_bytes(N, 8, 4)) / (f32["tmax_ms"] / f32["K"] * 1e-3) / 1e9, 1),
            "roofline": roofline(N, 8, 4, f32, "f32", hbm, hbm_kind),
            "precompute_ms": round(f32["precompute_ms"], 1), "plan_bytes": f32["plan_bytes"],
-           "gpu_launches": 5 * f32["K"], "clocks": f32["clocks"], "e2e": f32["e2e"]}
+           "gpu_launches": f32["launches"] * f32["K"], "clocks": f32["clocks"], "e2e": f32["e2e"]}
     t64 = f64["tmax_ms"] / f64["K"]
     out["fp64"] = {"value": round(f64["value"], 2), "unit": "solves/s",
                    "steps": f64["K"], "ms_per_step": round(t64, 4),
@@ -655,7 +656,7 @@ def main():
                                     "peak_kind": "nominal GB300 FP64 rate (a probe kernel measured 1.20)",
                                     "flops": "nominal 5 n log2 n per complex FFT of length n, pruned work counted "
                                              "as full"},
-                   "precompute_ms": round(f64["precompute_ms"], 1), "gpu_launches": 5 * f64["K"]}
+                   "precompute_ms": round(f64["precompute_ms"], 1), "gpu_launches": f64["launches"] * f64["K"]}
     tdf = fdf["tmax_ms"] / fdf["K"]
     out["fp64_df"] = {"value": round(fdf["value"], 2), "unit": "solves/s", "steps": fdf["K"], "ms_per_step": round(tdf, 4),
                       "p50_ms": round(float(np.percentile(fdf["per_step"], 50)), 4),
@@ -663,7 +664,7 @@ def main():
                       "hbm_gbs_solve": round(sum(pass_bytes(N, 16, 8)) / (tdf * 1e-3) / 1e9, 1),
                       "roofline": roofline(N, 16, 8, fdf, "f64df", hbm, hbm_kind),
                       "arithmetic": "double-float (float pairs) on the FP32 pipes, double arrays in and out",
-                      "gpu_launches": 5 * fdf["K"]}
+                      "gpu_launches": fdf["launches"] * fdf["K"]}
     out["field"] = field_leg(fsp, N, L, args.algo, max(10, K // 4), W, world)
     out["field"]["roofline"].update({"peak": hbm, "frac": round(out["field"]["roofline"]["achieved"] / hbm, 4),
                                      "peak_kind": hbm_kind + " copy bandwidth"})

@@ -246,6 +246,15 @@ fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents)
  * the environment variable FSP_GENERIC_ONLY=1 before fsp_plan_create forces
  * the generic engine (used to test both paths on the same sizes). */
 int fsp_plan_uses_fast_path(const fsp_plan *plan);
+/* Kernel launches per fsp_solve: 3 when the fused plane passes serve the
+ * plan (PA = pad + x-R2C + y-FFT of each z-plane in one thread-block
+ * cluster, P3, PC = y-IFFT + x-C2R + crops; the plane's intermediate W1 goes
+ * through L2 only), else 5 (Sec. 2.2 steps 1-5, one axis per launch).  The
+ * plane passes exist for FSP_F32_MIXED at N = 64, 128, 256 and are used by
+ * default at N = 64, where they measured faster; FSP_PLANE=1 (or 0) in the
+ * environment at plan creation forces them on (or off).  -1 for an invalid
+ * plan. */
+int fsp_plan_launches(const fsp_plan *plan);
 
 /* Device bytes the plan holds (spectrum + workspace + tables), 0 if invalid. */
 size_t fsp_plan_bytes(const fsp_plan *plan);

@@ -79,6 +79,8 @@ def lib(build_if_missing=True):
     L.fsp_solve_field.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fsp_plan_uses_fast_path.argtypes = [vp]
     L.fsp_plan_uses_fast_path.restype = i
+    L.fsp_plan_launches.argtypes = [vp]
+    L.fsp_plan_launches.restype = i
     L.fsp_plan_set_wait_timeout.argtypes = [vp, d]
     L.fsp_plan_inject_stall.argtypes = [vp]
     vpp = ctypes.POINTER(vp)
@@ -184,6 +186,11 @@ class Plan:
     def fast_path(self):
         """True when the specialised power-of-two kernels serve this plan."""
         return lib().fsp_plan_uses_fast_path(self._p) == 1
+
+    @property
+    def launches(self):
+        """Kernel launches per solve (3 with the fused plane passes, else 5)."""
+        return int(lib().fsp_plan_launches(self._p))
 
     @property
     def precompute_ms(self):

@@ -376,6 +376,7 @@ struct fsp_plan {
     TileCfg row, col;
     bool fast = false;  // specialised power-of-two kernels (fast.cuh) serve this N
     bool p3_tma = false;  // P3 by the TMA-staged persistent kernel (p3_tma.cuh)
+    bool plane = false;   // three launches: fused plane passes PA, PC around P3 (plane.cuh)
     unsigned *err = nullptr;  // device word: bit 0 = a bounded device-side wait timed out
     unsigned long long wait_timeout_ns = 1000000000ull;  // per device-side wait
     mutable std::atomic<unsigned> inject_tx{0};  // fault injection, consumed by the next solve
@@ -422,8 +423,40 @@ void plan_free(fsp_plan *p) {
     delete p;
 }
 
+// Three launches: PA (P1 + P2 per z-plane, W1 through L2 only), P3, PC (P4 +
+// P5 per z-plane).  The timing hook's six events then bracket PA as the first
+// pass and PC as the fourth (the second and fifth are empty).
+cudaError_t enqueue_solve_plane(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
+    const int N = p->N;
+    const long long P = p->P;
+    cudaError_t e;
+    auto mark = [&](int i) { return p->timing ? cudaEventRecord(p->ev[i], s) : cudaSuccess; };
+    fast::PlaneArgs pa{rho, phi, W1, W2, p->tw_n, p->tw_2n};
+    if ((e = mark(0)) != cudaSuccess) return e;
+    if ((e = fast::plane_fwd<float>(N, pa, s)) != cudaSuccess) return e;  // PA
+    if ((e = mark(1)) != cudaSuccess || (e = mark(2)) != cudaSuccess) return e;
+    fast::ColArgs a{};
+    a.tw = p->tw_2n, a.nlines = N + 1;
+    a.in = a.out = W2;  // P3: z-FFT * S * z-IFFT, in place, batch ky
+    a.in_pos = a.out_pos = 2LL * N * P, a.in_batch = a.out_batch = P;
+    a.S = p->S, a.s_pos = (long long)(N + 1) * P, a.s_batch = P, a.half = N;
+    if (p->p3_tma) {
+        fast::P3Wait w{p->err, p->wait_timeout_ns, p->inject_tx.exchange(0)};
+        e = fast::p3_tma<float>(N, W2, p->S, p->tw_2n, w, s);
+    } else {
+        e = fast::p3<float>(N, a, 2 * N, s);
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
+    if ((e = fast::plane_inv<float>(N, pa, s)) != cudaSuccess) return e;  // PC
+    if ((e = mark(4)) != cudaSuccess) return e;
+    return mark(5);
+}
+
 template <typename T>
 cudaError_t enqueue_solve_fast(const fsp_plan *p, const void *rho, void *phi, void *W1, void *W2, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value)
+        if (p->plane) return enqueue_solve_plane(p, rho, phi, W1, W2, s);
     const int N = p->N;
     const long long P = p->P;
     cudaError_t e;
@@ -814,6 +847,11 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
         // register-direct P3 on the GB300 (kept for the A/B and its tests)
         const char *t = std::getenv("FSP_P3_TMA");
         p->p3_tma = p->fast && dtype == FSP_F32_MIXED && fast::has_p3_tma<float>(N) && t && t[0] == '1';
+        // the fused plane passes where they measured faster; FSP_PLANE=1 / 0
+        // forces them on (every size that has them) / off, for the A/B
+        const char *pl = std::getenv("FSP_PLANE");
+        const bool plane_ok = p->fast && dtype == FSP_F32_MIXED && fast::has_plane<float>(N);
+        p->plane = plane_ok && (pl && pl[0] == '1' ? true : pl && pl[0] == '0' ? false : fast::plane_default<float>(N));
     }
     auto fail = [&](fsp_status e) {
         cudaStreamSynchronize(s);
@@ -1224,6 +1262,8 @@ fsp_status fsp_plan_inject_stall(fsp_plan *plan) {
 }
 
 int fsp_plan_uses_fast_path(const fsp_plan *plan) { return plan_live(plan) ? (plan->fast ? 1 : 0) : -1; }
+
+int fsp_plan_launches(const fsp_plan *plan) { return plan_live(plan) ? (plan->plane ? 3 : 5) : -1; }
 
 size_t fsp_plan_bytes(const fsp_plan *plan) { return plan_live(plan) ? plan->bytes : 0; }
 

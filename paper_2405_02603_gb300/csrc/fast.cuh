@@ -356,15 +356,7 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
         constexpr int X = NB / N;
         if ((int)blockIdx.y >= X) {
             line = blockIdx.x * L + l;
-            const int j = blockIdx.y - X;
-            if constexpr (G::ZL) {
-                // P3: k_y in the order 0, N, 1, 2N-1, 2, 2N-2, ...: the two
-                // rows that fold to the same spectrum row (k_y, 2N - k_y) are
-                // issued back to back, so the second finds S in L2
-                bt = j == 0 ? 0 : j == 1 ? N : (j & 1) ? 2 * N - ((j - 2) / 2 + 1) : (j - 2) / 2 + 1;
-            } else {
-                bt = j;
-            }
+            bt = blockIdx.y - X;
         } else {
             line = N;
             bt = ((long long)blockIdx.y * (N / L) + blockIdx.x) * L + l;

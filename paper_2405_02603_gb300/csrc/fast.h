@@ -64,6 +64,23 @@ struct P3Wait {
     unsigned extra_tx;
 };
 template <typename T> bool has_p3_tma(int N);
+
+// The fused plane passes (plane.cuh): PA = P1 + P2 and PC = P4 + P5 of each
+// z-plane in one thread-block cluster, W1 exchanged through L2 only.
+struct PlaneArgs {
+    const void *rho;    // PA: source, N^3 reals
+    void *phi;          // PC: result, N^3 reals (may be the source)
+    void *w1;           // W1[z][y][k_x], pitch P: the plane exchange (k_x = 0 packs X[0], X[N])
+    void *w2;           // W2[z][k_y][k_x], pitch P
+    const void *tw_n;   // roots of length N
+    const void *tw_2n;  // roots of length 2N
+};
+template <typename T> bool has_plane(int N);
+// the sizes whose plans use the plane passes by default (measured faster than
+// five launches on the GB300)
+template <typename T> bool plane_default(int N);
+template <typename T> cudaError_t plane_fwd(int N, const PlaneArgs &a, cudaStream_t s);
+template <typename T> cudaError_t plane_inv(int N, const PlaneArgs &a, cudaStream_t s);
 template <typename T> cudaError_t p3_tma(int N, void *w2, const void *S, const void *tw, const P3Wait &w, cudaStream_t s);
 
 }  // namespace fast

@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--algo", default="vg", choices=["he", "vg", "vg_dct"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-budget-s", type=float, default=90.0)
+    ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--no-systems", action="store_true", help="skip the batched and serving legs")
     ap.add_argument("--profile-case", default=None, metavar="DTYPES",
                     help="small profiling case instead of the bench: for each dtype in the comma-separated list "
@@ -502,32 +502,164 @@ def serving_leg(fsp, seconds=3.0, load=0.8, budget=100 << 30, slots=8):
                    % ",".join(map(str, SERVE_SIZES))}
 
 
+def numa_pages(addr, nbytes):
+    """{node: pages} of the mapping holding [addr, addr + nbytes), read from
+    /proc/self/maps and /proc/self/numa_maps (None when not available)."""
+    try:
+        maps = open("/proc/self/maps").read().splitlines()
+        numa = {int(ln.split()[0], 16): ln.split() for ln in open("/proc/self/numa_maps").read().splitlines()}
+    except (OSError, ValueError):
+        return None
+    out = {}
+    for ln in maps:
+        lo, hi = (int(v, 16) for v in ln.split()[0].split("-"))
+        if hi <= addr or lo >= addr + nbytes or lo not in numa:
+            continue
+        for f in numa[lo][1:]:
+            if f.startswith("N") and "=" in f:
+                k, v = f[1:].split("=")
+                out[int(k)] = out.get(int(k), 0) + int(v)
+    return out
+
+
+def copy_ceiling(host_in, host_out, nbytes, reps=30):
+    """Pinned host <-> device copy bandwidth of the e2e buffers: host-to-device
+    alone, device-to-host alone, and both at once on two streams (what the
+    pipelined solve needs every step); GB/s from CUDA events."""
+    import torch
+    n = len(host_in)
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    hin = [torch.from_numpy(h.view(np.uint8).reshape(-1)) for h in host_in]
+    hout = [torch.from_numpy(h.view(np.uint8).reshape(-1)) for h in host_out]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(h2d, d2h):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record(s1)
+        ev[2].record(s2)
+        for r in range(reps):
+            if h2d:
+                with torch.cuda.stream(s1):
+                    d_in.copy_(hin[r % n], non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    hout[r % n].copy_(d_out, non_blocking=True)
+        ev[1].record(s1)
+        ev[3].record(s2)
+        torch.cuda.synchronize()
+        return max(ev[0].elapsed_time(ev[1]) if h2d else 0.0, ev[2].elapsed_time(ev[3]) if d2h else 0.0)
+
+    run(True, True)  # warm-up
+    t_h2d, t_d2h, t_both = run(True, False), run(False, True), run(True, True)
+    gbs = lambda t: round(reps * nbytes / (t * 1e-3) / 1e9, 1)  # noqa: E731
+    return {"h2d_gbs": gbs(t_h2d), "d2h_gbs": gbs(t_d2h), "bidir_gbs_each_way": gbs(t_both),
+            "bidir_step_ms": round(t_both / reps, 4)}
+
+
 def e2e_leg(fsp, plan, host_src, dtype, K, W):
     """Same metric through the public host-buffer API: every step copies its
     source from pinned host memory to the device and its result back
     (fsp_solve_host_many, which overlaps step i's solve with the copies of
-    steps i+1 and i-1), timed on the wall clock."""
+    steps i+1 and i-1), timed on the wall clock.  The pinned buffers are
+    placed on the host NUMA node nearest the GPU (fsp_host_alloc); the copy
+    ceiling of the same buffers is measured beside it."""
     import torch
-    hsrc = torch.from_numpy(host_src.astype(np.float32 if dtype == "f32" else np.float64))
-    hin = [hsrc.clone().pin_memory() for _ in range(4)]
-    hout = [torch.empty_like(hsrc).pin_memory() for _ in range(4)]
-    rho = [hin[i % 4] for i in range(K)]
-    phi = [hout[i % 4] for i in range(K)]
+    npd = np.float32 if dtype == "f32" else np.float64
+    node = fsp.device_host_numa()
+    hb_in = [fsp.HostBuffer(host_src.shape, npd, node) for _ in range(4)]
+    hb_out = [fsp.HostBuffer(host_src.shape, npd, node) for _ in range(4)]
+    for b in hb_in:
+        b.array[...] = host_src.astype(npd)
+    rho = [hb_in[i % 4].array for i in range(K)]
+    phi = [hb_out[i % 4].array for i in range(K)]
     plan.solve_host_many(rho[:W], phi[:W])
     torch.cuda.synchronize()
     t = time.perf_counter()
     plan.solve_host_many(rho, phi)
     dt = time.perf_counter() - t
     t1 = time.perf_counter()
-    for i in range(max(4, K // 10)):
+    ns = max(4, K // 10)
+    for i in range(ns):
         plan.solve_host(rho[i], phi[i])
-    serial = max(4, K // 10) / (time.perf_counter() - t1)
-    nbytes = hsrc.numel() * hsrc.element_size()
-    return {"value": round(K / dt, 2), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "steps": K, "dtype": str(hsrc.dtype).replace("torch.", ""),
-            "path": "fsp_solve_host_many: pinned host rho -> device, solve, device -> pinned host phi per step, "
-                    "copies of neighbouring steps overlapped with each solve",
-            "unpipelined_value": round(serial, 2)}
+    serial = ns / (time.perf_counter() - t1)
+    nbytes = hb_in[0].nbytes
+    ceil = copy_ceiling([b.array for b in hb_in], [b.array for b in hb_out], nbytes)
+    ceil["solves_s_copy_bound"] = round(1e3 / ceil["bidir_step_ms"], 1)
+    pages = numa_pages(hb_in[0].array.ctypes.data, nbytes)
+    out = {"value": round(K / dt, 2), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": K, "dtype": np.dtype(npd).name,
+           "path": "fsp_solve_host_many: pinned host rho -> device, solve, device -> pinned host phi per step, "
+                   "copies of neighbouring steps overlapped with each solve",
+           "unpipelined_value": round(serial, 2), "copy_ceiling": ceil,
+           "numa": {"gpu_nearest_node": node, "buffer_pages_per_node": pages}}
+    for b in hb_in + hb_out:
+        b.close()
+    return out
+
+
+def precision_leg(fsp, Ns, L, W, world, with_oracle):
+    """The precision configuration at the sizes other than the bench's N:
+    VG-DCT solves of the seeded mixture (float32-rounded) in FP32-mixed, FP64
+    and double-float, each timed (solves/s) and compared with the oracle: the
+    whole field at N <= 256, at N = 512 the oracle's direct sum at 24 sampled
+    points (its full FFT solve takes minutes there) and the whole field
+    against this GPU's FP64 result."""
+    import torch
+    out = {}
+    for N in Ns:
+        rho = I.gaussian_mixture(N).astype(np.float32).astype(np.float64)
+        row, phis = {}, {}
+        for dtype, k in (("f32", 40 if N < 512 else 20), ("f64", 10 if N < 512 else 4), ("f64df", 20 if N < 512 else 8)):
+            plan = fsp.Plan(N, L, "vg_dct", dtype)
+            src = torch.from_numpy(rho).to(fsp.torch_dtype(dtype)).cuda()
+            dst = torch.empty_like(src)
+            for _ in range(W):
+                plan.solve_into(src, dst)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            barrier(world)
+            t0.record()
+            for _ in range(k):
+                plan.solve_into(src, dst)
+            t1.record()
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / k
+            row[dtype] = {"value": round(1e3 / ms, 2), "ms_per_solve": round(ms, 4), "steps": k}
+            phis[dtype] = dst.double().cpu().numpy()
+            plan.close()
+            del src, dst
+            torch.cuda.empty_cache()
+        if with_oracle:
+            import oracle
+            T = oracle.kernel_T("vg_dct", N, L)
+            if N <= 256:
+                ref = oracle.solve_fft(T, rho, L / N)
+                for d in row:
+                    row[d]["e_max_vs_oracle"] = e_max(phis[d], ref)
+                row["oracle"] = "whole field, full doubled-grid FFT solve"
+            else:
+                rng = np.random.default_rng(N)
+                pts = np.concatenate([rng.integers(0, N ** 3, 21), [0, N ** 3 - 1, (N // 2) * (N * N + N + 1)]])
+                ref = oracle.solve_direct(T, rho, L / N, pts)
+                for d in row:
+                    got = phis[d].ravel()[pts]
+                    row[d]["e_max_vs_oracle_sampled"] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+                for d in ("f32", "f64df"):
+                    row[d]["e_max_vs_gpu_f64"] = e_max(phis[d], phis["f64"])
+                row["oracle"] = "direct sum at 24 sampled points; whole field against the FP64 path"
+        out[str(N)] = row
+    return out
+
+
+def bench_config(N, L, algo, world):
+    """The workload's config object, the same in both arms of the bench."""
+    return {"workload": "VG free-space solve (Sec. 2.2 steps 1-5, Vico-Greengard spectrum), N=%d^3 "
+                        "cell-centred, unit cube" % N,
+            "N": N, "L": L, "algo": algo, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs rotate over %d source/output pairs; each solve streams ~%.2f GB, > 129 MB L2"
+                  % (NSRC, sum(pass_bytes(N, 8, 4)) / 1e9)}
 
 
 def cpu_oracle(N, L, rho, budget_s=None, max_solves=1):
@@ -574,12 +706,12 @@ def run_reference(args):
            "warmup": min(args.warmup, 1), "ms_per_step": round(1e3 * total / len(times), 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic: seeded 8-Gaussian mixture (seed 2405), float32-rounded",
-           "config": {"workload": "VG free-space solve, N=%d^3, unit cube, spectrum precomputed" % N,
-                      "N": N, "L": L, "algo": args.algo},
+           "config": bench_config(N, L, args.algo, 1),
            "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": oracle.num_threads(),
                             "kind": "oracle",
-                            "sample": "%d full N=%d solves (textbook FFT on the full (2N)^3 complex grid), "
-                                      "bounded to ~%.0f s" % (len(times), N, args.ref_budget_s)},
+                            "sample": "%d full N=%d solves (textbook FFT on the full (2N)^3 complex grid; "
+                                      "Vico-Greengard kernel by its DCT-I route, equal to the (4N)^3 route to "
+                                      "1e-13), bounded to ~%.0f s" % (len(times), N, args.ref_budget_s)},
            "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -618,7 +750,7 @@ def main():
         leg["launches"] = plan.launches
         leg["plan_bytes"] = plan.bytes
         leg["phi0"] = dsts[0].double().cpu().numpy() if rank == 0 else None
-        leg["e2e"] = e2e_leg(fsp, plan, host[0], dtype, max(20, k // 10), 3) if dtype == "f32" else None
+        leg["e2e"] = e2e_leg(fsp, plan, host[0], dtype, max(200, k), 5) if dtype == "f32" else None
         leg["value"], leg["tmax_ms"] = replica_value(k, leg["total_ms"], world)
         legs[dtype] = leg
         host0 = host[0]
@@ -631,11 +763,7 @@ def main():
            "n_gpus": world, "steps": f32["K"], "warmup": W, "ms_per_step": round(f32["tmax_ms"] / f32["K"], 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic: seeded 8-Gaussian mixtures (seeds 2405-2408), float32-rounded, no dataset",
-           "config": {"workload": "VG free-space solve (Sec. 2.2 steps 1-5, Vico-Greengard spectrum), N=%d^3 "
-                                  "cell-centred, unit cube" % N,
-                      "N": N, "L": L, "algo": args.algo, "parallelism": "replicas" if world > 1 else "single",
-                      "l2": "inputs rotate over %d source/output pairs; each solve streams ~%.2f GB, > 129 MB L2"
-                            % (NSRC, sum(pass_bytes(N, 8, 4)) / 1e9)},
+           "config": bench_config(N, L, args.algo, world),
            "p50_ms": round(float(np.percentile(f32["per_step"], 50)), 4),
            "p99_ms": round(float(np.percentile(f32["per_step"], 99)), 4),
            "hbm_gbs_solve": round(sum(pass_bytes(N, 8, 4)) / (f32["tmax_ms"] / f32["K"] * 1e-3) / 1e9, 1),
@@ -677,12 +805,33 @@ def main():
         out["cpu_baseline"] = {"value": round(1.0 / float(np.mean(times)), 5), "unit": "solves/s",
                                "cores": cores, "kind": "oracle",
                                "sample": "%d full N=%d VG solve(s) of source 0 (oracle: textbook FFT on the "
-                                         "full (2N)^3 complex grid, spectrum precomputed untimed)"
-                                         % (len(times), N)}
+                                         "full (2N)^3 complex grid, kernel by the DCT-I route, spectrum "
+                                         "precomputed untimed)" % (len(times), N)}
         out["e_max_vs_oracle"] = {"f32": e_max(f32["phi0"], phi_ref), "f64": e_max(f64["phi0"], phi_ref),
                                   "f64df": e_max(fdf["phi0"], phi_ref)}
         out["fp64"]["e_max_vs_oracle"] = out["e_max_vs_oracle"]["f64"]
         out["fp64_df"]["e_max_vs_oracle"] = out["e_max_vs_oracle"]["f64df"]
+    out["precision"] = precision_leg(fsp, (128, 512), L, W, world,
+                                     rank == 0 and world == 1 and not args.no_cpu_baseline)
+    if "e_max_vs_oracle" in out:
+        out["precision"][str(N)] = {d: {"value": round(legs[d]["value"], 2),
+                                        "e_max_vs_oracle": out["e_max_vs_oracle"][d]} for d in legs}
+        out["precision"][str(N)]["oracle"] = "whole field, full doubled-grid FFT solve (the cpu_baseline solve)"
+    # short scalar keys for the record (the objects above hold the details)
+    out["fp64_value"] = out["fp64"]["value"]
+    out["fp64_hbm_frac"] = out["fp64"]["roofline"]["frac"]
+    out["fp64_alu_frac"] = out["fp64"]["roofline_alu"]["frac"]
+    out["fp64_df_value"] = out["fp64_df"]["value"]
+    out["fp64_df_hbm_frac"] = out["fp64_df"]["roofline"]["frac"]
+    out["e2e_value"] = f32["e2e"]["value"]
+    out["e2e_copy_bound"] = f32["e2e"]["copy_ceiling"]["solves_s_copy_bound"]
+    for d in ("f32", "f64", "f64df"):
+        if "e_max_vs_oracle" in out:
+            out["e_max_%s_n%d" % (d, N)] = out["e_max_vs_oracle"][d]
+        for n in ("128", "512"):
+            r = out["precision"].get(n, {}).get(d, {})
+            if "e_max_vs_oracle" in r or "e_max_vs_oracle_sampled" in r:
+                out["e_max_%s_n%s" % (d, n)] = r.get("e_max_vs_oracle", r.get("e_max_vs_oracle_sampled"))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

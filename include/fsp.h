@@ -391,6 +391,22 @@ fsp_status fsp_autotune(int N, fsp_dtype dtype, fsp_stream stream, int *lgL_row,
 fsp_status fsp_tuning_get(char *buf, size_t cap, size_t *len);
 fsp_status fsp_tuning_set(const char *text);
 
+/* ------------------------------------------------------- host buffers --
+ * Pinned host memory for the host-buffer solves (fsp_solve_host,
+ * fsp_solve_host_many), placed on one host NUMA node.  The paper has no
+ * counterpart; its solver keeps its fields in device memory.
+ *
+ * fsp_device_host_numa: the host NUMA node closest to `device`
+ * (cudaDevAttrHostNumaId), -1 when unknown or the system has no NUMA.
+ * fsp_host_alloc: `bytes` of anonymous memory bound to `numa_node` (none when
+ * numa_node < 0), every page touched, then page-locked for the device.  The
+ * caller owns it and releases it with fsp_host_free(p, bytes).  FSP_ENOMEM
+ * when the mapping fails, FSP_EUNSUPPORTED when the node cannot be bound,
+ * FSP_ECUDA when page-locking fails. */
+int fsp_device_host_numa(int device);
+fsp_status fsp_host_alloc(void **out, size_t bytes, int numa_node);
+fsp_status fsp_host_free(void *p, size_t bytes);
+
 /*
  * fsp_solve_noalloc -- an FP64 solve that allocates no device memory.  The
  * paper has no counterpart: it is an interface for callers that cannot call

@@ -79,6 +79,12 @@ def lib(build_if_missing=True):
     L.fsp_solve_field.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fsp_plan_uses_fast_path.argtypes = [vp]
     L.fsp_plan_uses_fast_path.restype = i
+    L.fsp_device_host_numa.argtypes = [i]
+    L.fsp_device_host_numa.restype = i
+    L.fsp_host_alloc.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, i]
+    L.fsp_host_alloc.restype = i
+    L.fsp_host_free.argtypes = [vp, ctypes.c_size_t]
+    L.fsp_host_free.restype = i
     L.fsp_plan_launches.argtypes = [vp]
     L.fsp_plan_launches.restype = i
     L.fsp_plan_set_wait_timeout.argtypes = [vp, d]
@@ -476,3 +482,38 @@ def fft_c2c(x, sign=-1, stream=None):
 
 
 __all__ = ["autotune", "tuning_get", "tuning_set", "Plan", "Batch", "Server", "solve_batched", "FspError", "kernel_T", "fft_c2c", "solve_noalloc", "lib", "check", "library_path", "ALGOS", "DTYPES"]
+
+
+def device_host_numa(device=None):
+    """Host NUMA node closest to the GPU (-1 when unknown)."""
+    import torch
+    return int(lib().fsp_device_host_numa(torch.cuda.current_device() if device is None else int(device)))
+
+
+class HostBuffer:
+    """Pinned host memory bound to one NUMA node (fsp_host_alloc); `array`
+    is a numpy view of it (shape, dtype).  numa_node=None: the node nearest
+    the current GPU; -1: no binding."""
+
+    def __init__(self, shape, dtype, numa_node=None):
+        import numpy as np
+        self.dtype = np.dtype(dtype)
+        self.shape = tuple(shape)
+        self.nbytes = int(np.prod(self.shape)) * self.dtype.itemsize
+        self.numa_node = device_host_numa() if numa_node is None else int(numa_node)
+        self._p = ctypes.c_void_p()
+        check(lib().fsp_host_alloc(ctypes.byref(self._p), self.nbytes, self.numa_node), "fsp_host_alloc")
+        buf = (ctypes.c_char * self.nbytes).from_address(self._p.value)
+        self.array = np.frombuffer(buf, dtype=self.dtype).reshape(self.shape)
+
+    def close(self):
+        if self._p is not None and self._p.value:
+            self.array = None
+            check(lib().fsp_host_free(self._p, self.nbytes), "fsp_host_free")
+        self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

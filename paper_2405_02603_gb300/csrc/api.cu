@@ -552,11 +552,30 @@ cudaError_t enqueue_field_fast(const fsp_plan *p, const void *rho, void *const o
     cudaError_t e;
     fast::RowArgs r{};
     r.x = rho, r.c = p->W1, r.x_row = N, r.c_row = P, r.nrows = N * N, r.tw = p->tw_n, r.tw2 = p->tw_2n;
-    if ((e = fast::p1<T>(N, r, s)) != cudaSuccess) return e;
     fast::ColArgs a{};
     a.tw = p->tw_2n, a.nlines = N + 1;
     a.in = p->W1, a.out = p->W2;
     a.in_pos = P, a.in_batch = (long long)N * P, a.out_pos = P, a.out_batch = 2LL * N * P;
+    if constexpr (std::is_same<T, float>::value) {
+        if (p->plane) {  // the solve's own passes: PA once, then P3 and PC per output
+            fast::PlaneArgs pa{rho, nullptr, p->W1, p->W2, p->tw_n, p->tw_2n};
+            if ((e = fast::plane_fwd<float>(N, pa, s)) != cudaSuccess) return e;
+            for (int c = 3; c >= 0; --c) {
+                if (!out[c]) continue;
+                fast::ColArgs b = a;
+                b.in = p->W2, b.out = p->W3;
+                b.in_pos = b.out_pos = 2LL * N * P, b.in_batch = b.out_batch = P;
+                b.S = c == 3 ? p->S : p->SF[c], b.s_pos = (long long)(N + 1) * P, b.s_batch = P, b.half = N;
+                b.odd = c == 3 ? 0 : kP3Odd[c];
+                if ((e = c == 3 ? fast::p3<T>(N, b, 2 * N, s) : fast::p3_odd<T>(N, b, 2 * N, s)) != cudaSuccess)
+                    return e;
+                fast::PlaneArgs pc{nullptr, out[c], p->W1, p->W3, p->tw_n, p->tw_2n};
+                if ((e = fast::plane_inv<float>(N, pc, s)) != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
+    }
+    if ((e = fast::p1<T>(N, r, s)) != cudaSuccess) return e;
     if ((e = fast::p2<T>(N, a, N, s)) != cudaSuccess) return e;
     for (int c = 3; c >= 0; --c) {
         if (!out[c]) continue;

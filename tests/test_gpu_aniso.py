@@ -12,11 +12,10 @@ import numpy as np
 import pytest
 
 import fsp_inputs as I
-from conftest import e_max, to_dev
+from conftest import check_emax, e_max, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 2e-6}
 BOXES = [((12, 20, 9), (1.0, 1.25, 0.9)), ((16, 24, 40), (1.0, 1.0, 1.5)), ((2, 16, 8), (0.7, 1.0, 1.0)),
          ((24, 24, 48), (1.0, 1.0, 2.0)), ((30, 18, 25), (1.2, 0.9, 1.0))]
 
@@ -38,13 +37,11 @@ def test_aniso_whole_field(fsp, orc, n, L, algo, dtype):
     phi = p.solve(to_dev(rho, dtype)).cpu().numpy()
     ref = orc.solve_fft3(orc.kernel_T3(algo, n, h), rho, h)
     err = e_max(phi, ref)
-    print("aniso %s %s %s E_max %.2e" % (n, algo, dtype, err))
-    assert err <= TOL[dtype]
+    check_emax(err, max(n), dtype, "aniso-%s-%s" % ("x".join(map(str, n)), algo))
     p.close()
 
 
 FAST_BOXES = [((32, 64, 128), (1.0, 1.0, 2.0)), ((64, 32, 32), (1.2, 1.0, 0.8)), ((128, 32, 64), (1.0, 0.6, 0.8))]
-TOL3 = {"f64": 1e-12, "f32": 2e-6, "f64df": 1e-12}
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f64df"])
@@ -58,8 +55,7 @@ def test_aniso_fast_path(fsp, orc, n, L, algo, dtype):
     phi = p.solve(to_dev(rho, dtype)).cpu().numpy()
     ref = orc.solve_fft3(orc.kernel_T3(algo, n, h), rho, h)
     err = e_max(phi, ref)
-    print("aniso fast %s %s %s E_max %.2e" % (n, algo, dtype, err))
-    assert err <= TOL3[dtype]
+    check_emax(err, max(n), dtype, "aniso-fast-%s-%s" % ("x".join(map(str, n)), algo))
     p.close()
 
 
@@ -76,7 +72,7 @@ def test_aniso_fast_z_lines_of_2048(fsp, orc, algo):
     phi = p.solve(to_dev(rho, "f32")).cpu().numpy()
     p.close()
     ref = orc.solve_fft3(orc.kernel_T3(algo, n, h), rho, h)
-    assert e_max(phi, ref) <= TOL3["f32"]
+    check_emax(e_max(phi, ref), 1024, "f32", "aniso-z2048-%s" % algo)
     assert not fsp.Plan(n, L, algo, "f64").fast_path
 
 
@@ -153,8 +149,7 @@ def test_aniso_256x256x512_sampled(fsp, orc, dtype):
     pts = np.concatenate([rng.integers(0, tot, 12), [0, tot - 1, tot // 2 + n[0] * n[1] // 2 + n[0] // 2]])
     ref = orc.solve_direct3(orc.kernel_T3("he", n, h), rho, h, pts)
     err = float(np.max(np.abs(phi[pts] - ref)) / np.max(np.abs(ref)))
-    print("256x256x512 he %s sampled E_max %.2e" % (dtype, err))
-    assert err <= TOL3[dtype]
+    check_emax(err, 512, dtype, "aniso-256x256x512-he-sampled")
     p.close()
 
 
@@ -174,5 +169,4 @@ def test_aniso_512x512x1024_weak_scaling_shape(fsp, orc):
     pts = np.concatenate([rng.integers(0, tot, 4), [tot // 2 + n[0] * n[1] // 2 + n[0] // 2]])
     ref = orc.solve_direct3(orc.kernel_T3("he", n, h), rho.astype(np.float64), h, pts)
     err = float(np.max(np.abs(phi[pts] - ref)) / np.max(np.abs(ref)))
-    print("512x512x1024 he f32 sampled E_max %.2e" % err)
-    assert err <= TOL["f32"]
+    check_emax(err, 1024, "f32", "aniso-512x512x1024-he-sampled")

@@ -8,10 +8,9 @@ import numpy as np
 import pytest
 
 import fsp_inputs as I
-from conftest import e_max, oracle_T, to_dev
+from conftest import check_emax, e_max, oracle_T, to_dev
 
 pytestmark = pytest.mark.gpu
-TOL = {"f64": 1e-12, "f32": 2e-6}
 
 
 def _plan(fsp, N, algo, dtype, generic):
@@ -35,7 +34,7 @@ def test_fast_equals_generic(fsp, N, dtype):
     rho = to_dev(I.gaussian_mixture(N, seed=7).astype(np.float32), dtype)
     a = pf.solve(rho).double().cpu().numpy()
     b = pg.solve(rho).double().cpu().numpy()
-    assert e_max(a, b) <= TOL[dtype], e_max(a, b)
+    check_emax(e_max(a, b), N, dtype, "fast-vs-generic")
     pf.close()
     pg.close()
 
@@ -49,7 +48,7 @@ def test_fast_n128_against_oracle(fsp, orc, algo, dtype):
     assert p.fast_path
     phi = p.solve(to_dev(rho, dtype)).double().cpu().numpy()
     ref = orc.solve_fft(oracle_T(orc, algo, N), rho, 1.0 / N)
-    assert e_max(phi, ref) <= TOL[dtype], e_max(phi, ref)
+    check_emax(e_max(phi, ref), N, dtype, "fast-n128-%s" % algo)
     p.close()
 
 

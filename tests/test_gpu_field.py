@@ -14,11 +14,10 @@ import numpy as np
 import pytest
 
 import fsp_inputs as I
-from conftest import e_max, to_dev
+from conftest import check_emax, e_max, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 3e-6, "f64df": 1e-12}
 _F_CACHE = {}
 
 
@@ -51,8 +50,7 @@ def check_field(fsp, orc, algo, dtype, N, rho, L=1.0):
 def test_field_fast_path(fsp, orc, algo, dtype, N):
     rho = I.gaussian_mixture(N, seed=2405 + N)
     errs, same = check_field(fsp, orc, algo, dtype, N, rho)
-    print("field N=%d %s %s E_max per component %s" % (N, algo, dtype, ["%.2e" % e for e in errs]))
-    assert max(errs) <= TOL[dtype], errs
+    check_emax(max(errs), N, dtype, "field-fast-%s" % algo)
     assert same
 
 
@@ -62,7 +60,7 @@ def test_field_fast_path(fsp, orc, algo, dtype, N):
 def test_field_generic_engine(fsp, orc, algo, dtype, N):
     rho = I.random_field(N, 7 + N)
     errs, same = check_field(fsp, orc, algo, dtype, N, rho)
-    assert max(errs) <= TOL[dtype], errs
+    check_emax(max(errs), N, dtype, "field-generic-%s" % algo)
     assert same
 
 
@@ -72,7 +70,7 @@ def test_field_generic_engine_forced(fsp, orc, monkeypatch):
     monkeypatch.setenv("FSP_GENERIC_ONLY", "1")
     rho = I.gaussian_mixture(32, seed=9)
     errs, same = check_field(fsp, orc, "vg_dct", "f32", 32, rho)
-    assert max(errs) <= TOL["f32"], errs
+    check_emax(max(errs), 32, "f32", "field-generic-forced")
 
 
 def test_field_of_impulse_is_coulomb(fsp):
@@ -134,8 +132,7 @@ def test_field_n256_sampled_direct_sum(fsp, orc, dtype):
         ref = orc.solve_field_direct(F[a], a, rho, h, pts)
         got = out[a].cpu().numpy().ravel()[pts]
         err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
-        print("N=256 vg %s field component %d sampled E_max = %.3e" % (dtype, a, err))
-        assert err <= TOL[dtype]
+        check_emax(err, N, dtype, "field-n256-sampled-%d" % a)
     p.close()
 
 
@@ -161,8 +158,7 @@ def test_field_noncubic(fsp, orc, n, L, dtypes, algo):
         p = fsp.Plan(n, L, algo, dtype)
         out = p.solve_field(to_dev(rho, dtype), with_phi=True)
         errs = [e_max(out[a].cpu().numpy(), refs[a]) for a in range(3)]
-        print("field %s %s %s fast=%s E_max %s" % (n, algo, dtype, p.fast_path, ["%.2e" % e for e in errs]))
-        assert max(errs) <= TOL[dtype], errs
+        check_emax(max(errs), max(n), dtype, "field-%s-%s" % ("x".join(map(str, n)), algo))
         assert bool((out[3] == p.solve(to_dev(rho, dtype))).all())
         p.close()
 

@@ -14,11 +14,10 @@ import numpy as np
 import pytest
 
 import fsp_inputs as I
-from conftest import e_max, to_dev
+from conftest import check_emax, e_max, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 2e-6, "f64df": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -36,8 +35,7 @@ def test_n256_full_field(fsp, ref256, algo, dtype):
     p = fsp.Plan(N, L, algo, dtype)
     phi = p.solve(to_dev(rho, dtype)).cpu().numpy()
     err = e_max(phi, ref)
-    print("N=256 %s %s E_max vs oracle = %.3e" % (algo, dtype, err))
-    assert err <= TOL[dtype]
+    check_emax(err, N, dtype, "fullsize-%s" % algo)
     p.close()
 
 
@@ -53,8 +51,7 @@ def test_n512_he_sampled_direct_sum(fsp, orc, dtype):
     T = orc.kernel_T("he", N, L)
     ref = orc.solve_direct(T, rho, h, pts)
     err = float(np.max(np.abs(phi[pts] - ref)) / np.max(np.abs(ref)))
-    print("N=512 he %s sampled E_max vs direct sum = %.3e" % (dtype, err))
-    assert err <= TOL[dtype]
+    check_emax(err, N, dtype, "n512-he-sampled")
     p.close()
 
 

@@ -8,10 +8,9 @@ import numpy as np
 import pytest
 
 import fsp_inputs as I
-from conftest import to_dev
+from conftest import check_emax, to_dev
 
 pytestmark = pytest.mark.gpu
-TOL = {"f64": 1e-12, "f32": 2e-6}
 
 
 @pytest.mark.parametrize("N,dtype", [(1024, "f32"), (1024, "f64"), (768, "f64")])
@@ -30,8 +29,7 @@ def test_largest_grids_against_direct_sums(fsp, orc, N, dtype):
     pts = np.concatenate([rng.integers(0, N ** 3, 10), [0, N ** 3 - 1]])
     ref = orc.solve_direct(orc.kernel_T("he", N, L), rho, h, pts)
     err = float(np.max(np.abs(phi[pts] - ref)) / np.max(np.abs(ref)))
-    print("N=%d %s sampled E_max vs direct sum %.3e" % (N, dtype, err))
-    assert err <= TOL[dtype]
+    check_emax(err, N, dtype, "maxsize-sampled")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f64df"])

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import fsp_inputs as I
-from conftest import e_max, to_dev
+from conftest import check_emax, e_max, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -57,8 +57,7 @@ def test_tma_p3_n64_matches_oracle(fsp, orc, algo):
     phi = p.solve(to_dev(rho, "f32")).double().cpu().numpy()
     p.sync()
     err = e_max(phi, ref)
-    print("N=64 %s TMA P3 E_max vs oracle %.3e" % (algo, err))
-    assert err <= 2e-6
+    check_emax(err, N, "f32", "p3tma-%s" % algo)
     p.close()
 
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import fsp_inputs as I
-from conftest import e_max, to_dev
+from conftest import check_emax, e_max, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +63,7 @@ def test_plane_matches_oracle(fsp, orc, N, algo):
     p = _plan(fsp, N, algo, True)
     phi = p.solve(to_dev(rho, "f32")).double().cpu().numpy()
     err = e_max(phi, ref)
-    print("N=%d %s plane schedule E_max vs oracle %.3e" % (N, algo, err))
-    assert err <= 2e-6
+    check_emax(err, N, "f32", "plane-%s" % algo)
     p.close()
 
 

@@ -391,6 +391,42 @@ fsp_status fsp_autotune(int N, fsp_dtype dtype, fsp_stream stream, int *lgL_row,
 fsp_status fsp_tuning_get(char *buf, size_t cap, size_t *len);
 fsp_status fsp_tuning_set(const char *text);
 
+/* ---------------------------------------------- slab-decomposed solve --
+ * One rank's share of a solve distributed over R ranks (the paper's
+ * distributed solver transposes pencils with all-to-all exchanges, Sec. 3.2;
+ * the physical grid maps onto the doubled one as in Appendix A, Algorithm 1).
+ * Rank r owns the z-planes [z0, z1) of rho and phi (dense slabs of
+ * (z1-z0) N^2 reals, C order as for fsp_solve) and the half-spectrum columns
+ * k_x in [kx0, kx1), with z0 = floor(r N / R), kx0 = floor(r (N+1) / R).
+ * A solve is
+ *   fsp_dist_forward   P1 and P2 on the z-slab; writes send block q for every
+ *                      rank q (phase 0);
+ *   (caller)           block r -> q of every pair is copied into q's receive
+ *                      block from r (an all-to-all: NCCL, peer copies, or
+ *                      device copies when the ranks share a process);
+ *   fsp_dist_middle    assembles the k_x slab from the phase-0 receive blocks,
+ *                      P3 and P4 on it; writes the phase-1 send blocks;
+ *   (caller)           the phase-1 all-to-all;
+ *   fsp_dist_backward  assembles the z-slab's rows, P5 into phi.
+ * Blocks are the caller's device arrays of fsp_dist_block_elems complex
+ * values (double2 for FSP_F64, float2 for FSP_F32_MIXED), 16-byte aligned,
+ * one per peer (including the rank itself), indexed by peer rank.  Phase-0
+ * block s -> q: [zl][k_y][j], zl < nz_s, k_y < 2N, j < kx-width of q.
+ * Phase-1 block s -> q: [zl][y][j], zl < nz_q, y < N, j < kx-width of s.
+ * Generic engine (2N 2/3/5-smooth, 4N for FSP_VG), FSP_F64 or
+ * FSP_F32_MIXED (else FSP_EUNSUPPORTED); 1 <= R <= N.  Asynchronous on
+ * `stream`.  fsp_dist_partition and fsp_dist_block_elems are host arithmetic
+ * only (no device); fsp_dist_block_elems returns -1 for invalid arguments. */
+typedef struct fsp_dist fsp_dist;
+fsp_status fsp_dist_partition(int N, int nranks, int rank, int *z0, int *z1, int *kx0, int *kx1);
+long long fsp_dist_block_elems(int N, int nranks, int rank, int phase, int peer, int sending);
+fsp_status fsp_dist_create(fsp_dist **out, int N, double L, fsp_algo algo, fsp_dtype dtype, int nranks, int rank,
+                           fsp_stream stream);
+fsp_status fsp_dist_forward(fsp_dist *d, const void *rho_slab, void *const *send, fsp_stream stream);
+fsp_status fsp_dist_middle(fsp_dist *d, const void *const *recv, void *const *send, fsp_stream stream);
+fsp_status fsp_dist_backward(fsp_dist *d, const void *const *recv, void *phi_slab, fsp_stream stream);
+fsp_status fsp_dist_destroy(fsp_dist *d);
+
 /* ------------------------------------------------------- host buffers --
  * Pinned host memory for the host-buffer solves (fsp_solve_host,
  * fsp_solve_host_many), placed on one host NUMA node.  The paper has no

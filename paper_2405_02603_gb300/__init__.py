@@ -79,6 +79,20 @@ def lib(build_if_missing=True):
     L.fsp_solve_field.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fsp_plan_uses_fast_path.argtypes = [vp]
     L.fsp_plan_uses_fast_path.restype = i
+    L.fsp_dist_partition.argtypes = [i, i, i] + [ctypes.POINTER(i)] * 4
+    L.fsp_dist_partition.restype = i
+    L.fsp_dist_block_elems.argtypes = [i, i, i, i, i, i]
+    L.fsp_dist_block_elems.restype = ctypes.c_longlong
+    L.fsp_dist_create.argtypes = [ctypes.POINTER(vp), i, d, i, i, i, i, vp]
+    L.fsp_dist_create.restype = i
+    L.fsp_dist_forward.argtypes = [vp, vp, ctypes.POINTER(vp), vp]
+    L.fsp_dist_forward.restype = i
+    L.fsp_dist_middle.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.fsp_dist_middle.restype = i
+    L.fsp_dist_backward.argtypes = [vp, ctypes.POINTER(vp), vp, vp]
+    L.fsp_dist_backward.restype = i
+    L.fsp_dist_destroy.argtypes = [vp]
+    L.fsp_dist_destroy.restype = i
     L.fsp_device_host_numa.argtypes = [i]
     L.fsp_device_host_numa.restype = i
     L.fsp_host_alloc.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, i]
@@ -517,3 +531,119 @@ class HostBuffer:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------- slab-decomposed solve --
+def dist_partition(N, nranks, rank):
+    """(z0, z1, kx0, kx1): the z-planes and half-spectrum columns of a rank."""
+    v = [ctypes.c_int() for _ in range(4)]
+    check(lib().fsp_dist_partition(int(N), int(nranks), int(rank), *[ctypes.byref(x) for x in v]),
+          "fsp_dist_partition")
+    return tuple(x.value for x in v)
+
+
+def dist_block_elems(N, nranks, rank, phase, peer, sending):
+    """Complex values of the block `rank` sends to (or receives from) `peer`."""
+    n = int(lib().fsp_dist_block_elems(int(N), int(nranks), int(rank), int(phase), int(peer), int(bool(sending))))
+    if n < 0:
+        raise FspError(FSP_EINVAL, "fsp_dist_block_elems")
+    return n
+
+
+class DistPlan:
+    """One rank's share of a slab-decomposed solve (fsp_dist_*).  The caller
+    moves the blocks between ranks: `exchange_local` for ranks of one process,
+    torch.distributed all-to-all for ranks on several GPUs."""
+
+    def __init__(self, N, L=1.0, algo="vg_dct", dtype="f64", nranks=1, rank=0, stream=None):
+        self.N, self.L, self.dtype, self.R, self.rank = int(N), float(L), dtype, int(nranks), int(rank)
+        self._d = ctypes.c_void_p()
+        check(lib().fsp_dist_create(ctypes.byref(self._d), self.N, self.L, _algo_code(algo), _dtype_code(dtype),
+                                    self.R, self.rank, _stream_handle(stream)), "fsp_dist_create")
+        self.z0, self.z1, self.kx0, self.kx1 = dist_partition(self.N, self.R, self.rank)
+
+    def blocks(self, phase, sending):
+        """Fresh device blocks of this rank for one phase, indexed by peer."""
+        import torch
+        ct = torch.complex128 if self.dtype == "f64" else torch.complex64
+        return [torch.empty(max(1, dist_block_elems(self.N, self.R, self.rank, phase, q, sending)), dtype=ct,
+                            device="cuda") for q in range(self.R)]
+
+    def forward(self, rho_slab, send, stream=None):
+        check(lib().fsp_dist_forward(self._d, ctypes.c_void_p(rho_slab.data_ptr()),
+                                     _ptr_array([t.data_ptr() for t in send]), _stream_handle(stream)),
+              "fsp_dist_forward")
+
+    def middle(self, recv, send, stream=None):
+        check(lib().fsp_dist_middle(self._d, _ptr_array([t.data_ptr() for t in recv]),
+                                    _ptr_array([t.data_ptr() for t in send]), _stream_handle(stream)),
+              "fsp_dist_middle")
+
+    def backward(self, recv, phi_slab, stream=None):
+        check(lib().fsp_dist_backward(self._d, _ptr_array([t.data_ptr() for t in recv]),
+                                      ctypes.c_void_p(phi_slab.data_ptr()), _stream_handle(stream)),
+              "fsp_dist_backward")
+
+    def close(self):
+        if self._d is not None and self._d.value:
+            check(lib().fsp_dist_destroy(self._d), "fsp_dist_destroy")
+        self._d = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def exchange_local(sends, recvs):
+    """The all-to-all of ranks that share one process: recvs[q][r] = sends[r][q]."""
+    for r, row in enumerate(sends):
+        for q, blk in enumerate(row):
+            recvs[q][r].copy_(blk)
+
+
+def solve_distributed_local(N, rho, L=1.0, algo="vg_dct", dtype="f64", nranks=2):
+    """Emulate `nranks` ranks in this process on the current GPU: split rho
+    (device, N^3) into z-slabs, run the three phases with device-to-device
+    exchanges, gather phi."""
+    import torch
+    ranks = [DistPlan(N, L, algo, dtype, nranks, r) for r in range(nranks)]
+    phi = torch.empty_like(rho)
+    send0 = [p.blocks(0, True) for p in ranks]
+    recv0 = [p.blocks(0, False) for p in ranks]
+    for p, snd in zip(ranks, send0):
+        p.forward(rho[p.z0:p.z1].clone(), snd)  # a fresh, aligned slab
+    exchange_local(send0, recv0)
+    send1 = [p.blocks(1, True) for p in ranks]
+    recv1 = [p.blocks(1, False) for p in ranks]
+    for p, rcv, snd in zip(ranks, recv0, send1):
+        p.middle(rcv, snd)
+    exchange_local(send1, recv1)
+    for p, rcv in zip(ranks, recv1):
+        out = torch.empty((p.z1 - p.z0,) + tuple(rho.shape[1:]), dtype=rho.dtype, device=rho.device)
+        p.backward(rcv, out)
+        phi[p.z0:p.z1] = out
+    torch.cuda.synchronize()
+    for p in ranks:
+        p.close()
+    return phi
+
+
+def exchange_dist(sends, recvs, group=None):
+    """The all-to-all of one rank among processes: recvs[q] receives rank q's
+    block for this rank, sends[q] goes to rank q (torch.distributed point-to-
+    point: NCCL for device blocks, gloo for host blocks)."""
+    import torch
+    import torch.distributed as dist
+    me, R = dist.get_rank(group), dist.get_world_size(group)
+    real = lambda t: torch.view_as_real(t) if t.is_complex() else t  # noqa: E731
+    works = []
+    for q in range(R):
+        if q == me:
+            recvs[q].copy_(sends[q])
+            continue
+        works.append(dist.isend(real(sends[q]).contiguous(), q, group=group))
+        works.append(dist.irecv(real(recvs[q]), q, group=group))
+    for w in works:
+        w.wait()

@@ -30,6 +30,7 @@
 #include "greens.h"
 #include "kernels.cuh"
 #include "tiles.h"
+#include "internal.h"
 
 using namespace fsp;
 
@@ -929,6 +930,23 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     return FSP_OK;
 }
 }  // namespace
+
+namespace fsp {
+namespace internal {
+
+fsp_status spectrum_plan_create(fsp_plan **out, int N, double L, fsp_algo algo, fsp_dtype dtype, cudaStream_t s) {
+    return plan_create_impl(out, N, L, L / N, algo, dtype, reinterpret_cast<fsp_stream>(s), false);
+}
+
+bool plan_view(const fsp_plan *p, PlanView *v) {
+    if (!plan_live(p) || !v || p->aniso) return false;
+    v->N = p->N, v->P = p->P, v->device = p->device, v->dtype = p->dtype, v->rsize = p->rsize;
+    v->S = p->S, v->tw_n = p->tw_n, v->tw_2n = p->tw_2n, v->row = p->row, v->col = p->col;
+    return true;
+}
+
+}  // namespace internal
+}  // namespace fsp
 
 extern "C" {
 

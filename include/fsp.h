@@ -340,11 +340,16 @@ fsp_status fsp_solve_batched(fsp_plan *const *plans, const void *const *rho, voi
  * paper).  A worker thread owned by the server admits queued requests into
  * free slots (one CUDA stream each) as soon as a slot and device memory are
  * free, so solves of different sizes overlap on the device.  Spectra are
- * cached per (N, L, algo, dtype) and evicted least-recently-used; spectra,
- * workspaces and cached plans together never exceed the budget.  Every solve
- * uses the same kernels as fsp_solve, so a result is bitwise the same alone
- * or in a mix.  A cache miss builds the spectrum synchronously in the worker
- * (other requests wait meanwhile).
+ * cached per (N, L, algo, dtype) and evicted least-recently-used.  A cache
+ * miss is built by a second server thread on its own stream, outside the
+ * worker's lock: meanwhile the worker keeps admitting (FIFO among requests
+ * whose spectrum is ready; requests waiting for a build keep their place
+ * without holding back the ones behind them) and retiring solves.  Spectra,
+ * workspaces and the temporaries of builds in progress (the kernel on the
+ * (4N)^3 grid for FSP_VG, the (2N+1)^3 octant for FSP_VG_DCT, reserved before
+ * a build starts) together never exceed the budget; a request that cannot fit
+ * with nothing else running fails with FSP_ENOMEM.  Every solve uses the same
+ * kernels as fsp_solve, so a result is bitwise the same alone or in a mix.
  */
 typedef struct fsp_server fsp_server;
 
@@ -354,6 +359,8 @@ typedef struct {
     uint64_t queued, running;
     uint64_t cached_spectra;
     size_t bytes_in_use, budget;
+    uint64_t builds_in_flight;  /* spectra being built now */
+    size_t peak_bytes_in_use;   /* the most bytes_in_use has been */
 } fsp_server_stats;
 
 /* hbm_budget_bytes > 0; 1 <= max_slots <= 64 (concurrent solves). */

@@ -28,7 +28,8 @@ class ServerStats(ctypes.Structure):
     """fsp_server_stats"""
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "spec_hits", "spec_misses",
                                                "evictions", "queued", "running", "cached_spectra")] + \
-               [("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t)]
+               [("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t),
+                ("builds_in_flight", ctypes.c_uint64), ("peak_bytes_in_use", ctypes.c_size_t)]
 
 
 class FspError(RuntimeError):

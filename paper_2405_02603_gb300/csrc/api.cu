@@ -1748,10 +1748,27 @@ struct fsp_server {
     uint64_t next_ticket = 1;
     struct Spec {
         fsp_plan *plan = nullptr;
-        size_t bytes = 0;
+        size_t bytes = 0;     // held in the budget: the plan's, or the build's reservation
         uint64_t last_use = 0;
         int refs = 0;
+        bool ready = true;    // false while the builder thread computes it
+        fsp_status status = FSP_OK;  // the build's result
     };
+    // spectra missing from the cache are built by a thread of their own, on
+    // its own stream, without the worker's lock: admission and retirement of
+    // other requests go on meanwhile
+    struct Build {
+        std::tuple<int, uint64_t, int, int> key;
+        int N;
+        double L;
+        fsp_algo algo;
+        fsp_dtype dtype;
+    };
+    std::deque<Build> builds;
+    std::thread builder;
+    cudaStream_t build_stream = nullptr;
+    int builds_in_flight = 0;
+    size_t peak = 0;
     std::map<std::tuple<int, uint64_t, int, int>, Spec> specs;
     struct WS {
         void *W1 = nullptr, *W2 = nullptr;
@@ -1789,6 +1806,26 @@ uint64_t bits_of(double x) {
     return u;
 }
 
+// Device bytes a spectrum-only plan holds once built (spectrum, roots tables,
+// error word), and the peak of the temporaries its creation allocates (the
+// real-space kernel and the method's sample grid with its transform buffers).
+size_t spec_bytes(int N, fsp_dtype dtype) {
+    const size_t P = ((N + 1) + 15) / 16 * 16, rs = dtype == FSP_F32_MIXED ? 4 : 8;
+    return (size_t)(N + 1) * (N + 1) * P * rs + 3 * (size_t)N * 2 * rs + 16;
+}
+size_t plan_temp_bytes(int N, fsp_algo algo) {
+    const size_t k = N + 1;
+    size_t b = k * k * k * sizeof(double) + (size_t)64 * 1024 + 48 * (size_t)N;  // kernel T, roots
+    if (algo == FSP_VG_DCT) {
+        const size_t q = 2 * (size_t)N + 1;  // the (2N+1)^3 octant and its two pruned transforms
+        b += (q * q * q + q * q * k + q * k * k) * sizeof(double);
+    } else if (algo == FSP_VG) {
+        const size_t m = 4 * (size_t)N;  // the (4N)^3 complex grid and its two pruned transforms
+        b += (m * m * m + m * m * k + m * k * k) * sizeof(double2);
+    }
+    return b;
+}
+
 size_t ws_bytes(int N, fsp_dtype dtype) {
     const size_t P = ((N + 1) + 15) / 16 * 16;
     return (size_t)N * N * P * (dtype == FSP_F32_MIXED ? 8 : 16) * 3;
@@ -1807,10 +1844,11 @@ bool server_make_room(fsp_server *v, size_t need) {
     while (v->used + need > v->budget) {
         auto victim = v->specs.end();
         for (auto it = v->specs.begin(); it != v->specs.end(); ++it)
-            if (it->second.refs == 0 && (victim == v->specs.end() || it->second.last_use < victim->second.last_use))
+            if (it->second.refs == 0 && it->second.ready &&
+                (victim == v->specs.end() || it->second.last_use < victim->second.last_use))
                 victim = it;
         if (victim == v->specs.end()) return false;
-        fsp_plan_destroy(victim->second.plan);
+        if (victim->second.plan) fsp_plan_destroy(victim->second.plan);
         v->used -= victim->second.bytes;
         v->specs.erase(victim);
         v->st.evictions++;
@@ -1848,15 +1886,10 @@ void server_loop(fsp_server *v) {
                 if (x.busy) return false;
             return true;
         };
-        // a request that cannot fit even with nothing running fails with ENOMEM
-        auto fail_front = [&](fsp_status why) {
-            auto &r = v->reqs[v->queue.front()];
-            r.state = 3, r.status = why, r.t_done = std::chrono::steady_clock::now();
-            v->queue.pop_front();
-            v->st.completed++;
-            progress = true;
-        };
-        while (!v->queue.empty()) {
+        // FIFO over the requests whose spectrum is ready; a request whose
+        // spectrum is still being built keeps its place without holding back
+        // the ones behind it
+        for (size_t qi = 0; qi < v->queue.size();) {
             int si = -1;
             for (int i = 0; i < (int)v->slots.size(); ++i)
                 if (!v->slots[i].busy) {
@@ -1864,40 +1897,51 @@ void server_loop(fsp_server *v) {
                     break;
                 }
             if (si < 0) break;
-            const uint64_t t = v->queue.front();
+            const uint64_t t = v->queue[qi];
             auto &r = v->reqs[t];
             auto key = std::make_tuple(r.N, bits_of(r.L), (int)r.algo, (int)r.dtype);
+            auto fail_at = [&](fsp_status why) {
+                r.state = 3, r.status = why, r.t_done = std::chrono::steady_clock::now();
+                v->queue.erase(v->queue.begin() + qi);
+                v->st.completed++;
+                progress = true;
+            };
             auto it = v->specs.find(key);
             if (it == v->specs.end()) {
-                // spectrum-only plan; its size is known before it is built
-                const size_t P = ((r.N + 1) + 15) / 16 * 16;
-                const size_t rs = r.dtype == FSP_F32_MIXED ? 4 : 8;
-                const size_t need = (size_t)(r.N + 1) * (r.N + 1) * P * rs + 3 * (size_t)r.N * 2 * rs;
-                if (!server_make_room(v, need)) {  // wait for running solves to release memory
-                    if (none_busy()) {
-                        fail_front(FSP_ENOMEM);
+                // reserve the spectrum and its build's temporaries, then hand
+                // the build to the builder thread
+                const size_t need = spec_bytes(r.N, r.dtype) + plan_temp_bytes(r.N, r.algo);
+                if (!server_make_room(v, need)) {
+                    if (none_busy() && v->builds_in_flight == 0) {
+                        fail_at(FSP_ENOMEM);  // cannot fit even with nothing running
                         continue;
                     }
-                    break;
-                }
-                fsp_plan *p = nullptr;
-                const fsp_status cs = plan_create_impl(&p, r.N, r.L, r.L / r.N, r.algo, r.dtype,
-                                                       reinterpret_cast<fsp_stream>(v->slots[si].stream), false);
-                if (cs != FSP_OK) {
-                    r.state = 3, r.status = cs, r.t_done = std::chrono::steady_clock::now();
-                    v->queue.pop_front();
-                    v->st.completed++;
-                    progress = true;
-                    continue;
+                    break;  // wait for running solves and builds to release memory
                 }
                 fsp_server::Spec sp;
-                sp.plan = p, sp.bytes = p->bytes;
-                v->used += sp.bytes;
-                it = v->specs.emplace(key, sp).first;
+                sp.ready = false, sp.bytes = need, sp.last_use = ++v->clock;
+                v->used += need;
+                v->peak = std::max(v->peak, v->used);
+                v->specs.emplace(key, sp);
+                v->builds.push_back({key, r.N, r.L, r.algo, r.dtype});
+                v->builds_in_flight++;
                 v->st.spec_misses++;
-            } else {
-                v->st.spec_hits++;
+                v->cv.notify_all();
+                progress = true;
+                ++qi;
+                continue;
             }
+            if (!it->second.ready) {  // being built: look further down the queue
+                ++qi;
+                continue;
+            }
+            if (it->second.status != FSP_OK) {  // the build failed: so does every request for it
+                const fsp_status why = it->second.status;
+                if (it->second.refs == 0) v->specs.erase(it);
+                fail_at(why);
+                continue;
+            }
+            v->st.spec_hits++;
             it->second.refs++;  // pinned while a workspace is sought
             fsp_server::WS ws;
             bool have = false;
@@ -1912,8 +1956,8 @@ void server_loop(fsp_server *v) {
                 const size_t wb = ws_bytes(r.N, r.dtype);
                 if (!server_make_room(v, wb)) {
                     it->second.refs--;
-                    if (none_busy()) {
-                        fail_front(FSP_ENOMEM);
+                    if (none_busy() && v->builds_in_flight == 0) {
+                        fail_at(FSP_ENOMEM);
                         continue;
                     }
                     break;
@@ -1924,20 +1968,21 @@ void server_loop(fsp_server *v) {
                     if (ws.W1) cudaFree(ws.W1);
                     ws.W1 = nullptr;
                     it->second.refs--;
-                    if (none_busy()) {
-                        fail_front(FSP_ENOMEM);
+                    if (none_busy() && v->builds_in_flight == 0) {
+                        fail_at(FSP_ENOMEM);
                         continue;
                     }
                     break;
                 }
                 ws.bytes = wb, ws.N = r.N, ws.dtype = r.dtype;
                 v->used += wb;
+                v->peak = std::max(v->peak, v->used);
             }
             auto &sl = v->slots[si];
             it->second.last_use = ++v->clock;
             const cudaError_t e = enqueue_solve_ws(it->second.plan, r.rho, r.phi, ws.W1, ws.W2, sl.stream);
             const cudaError_t e2 = e == cudaSuccess ? cudaEventRecord(sl.ev, sl.stream) : e;
-            v->queue.pop_front();
+            v->queue.erase(v->queue.begin() + qi);
             if (e2 != cudaSuccess) {
                 cudaGetLastError();
                 r.state = 3, r.status = FSP_ECUDA, r.t_done = std::chrono::steady_clock::now();
@@ -1961,6 +2006,34 @@ void server_loop(fsp_server *v) {
         } else {
             v->cv.wait_for(lk, std::chrono::milliseconds(2));
         }
+    }
+}
+
+// The builder thread: builds queued spectra on its own stream, outside the
+// worker's lock, then swaps the build's reservation in the budget for the
+// plan's actual size.
+void server_build_loop(fsp_server *v) {
+    cudaSetDevice(v->device);
+    std::unique_lock<std::mutex> lk(v->mu);
+    while (!v->stop) {
+        if (v->builds.empty()) {
+            v->cv.wait_for(lk, std::chrono::milliseconds(20));
+            continue;
+        }
+        const fsp_server::Build b = v->builds.front();
+        v->builds.pop_front();
+        lk.unlock();
+        fsp_plan *p = nullptr;
+        const fsp_status cs = plan_create_impl(&p, b.N, b.L, b.L / b.N, b.algo, b.dtype,
+                                               reinterpret_cast<fsp_stream>(v->build_stream), false);
+        lk.lock();
+        auto &sp = v->specs[b.key];
+        v->used -= sp.bytes;
+        sp.status = cs, sp.ready = true, sp.plan = cs == FSP_OK ? p : nullptr;
+        sp.bytes = cs == FSP_OK ? p->bytes : 0;
+        v->used += sp.bytes;
+        v->builds_in_flight--;
+        v->cv.notify_all();
     }
 }
 
@@ -1988,8 +2061,14 @@ extern "C" fsp_status fsp_server_create(fsp_server **out, size_t hbm_budget_byte
             return FSP_ECUDA;
         }
     }
+    if (cudaStreamCreateWithFlags(&v->build_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        for (auto &x : v->slots) cudaStreamDestroy(x.stream), cudaEventDestroy(x.ev);
+        delete v;
+        return FSP_ECUDA;
+    }
     v->magic = kServerMagic;
     v->worker = std::thread(server_loop, v);
+    v->builder = std::thread(server_build_loop, v);
     {
         std::lock_guard<std::mutex> lk(g_mu);
         g_servers.insert(v);
@@ -2047,6 +2126,8 @@ extern "C" fsp_status fsp_server_get_stats(fsp_server *v, fsp_server_stats *out)
     out->bytes_in_use = v->used;
     out->budget = v->budget;
     out->cached_spectra = v->specs.size();
+    out->builds_in_flight = (uint64_t)v->builds_in_flight;
+    out->peak_bytes_in_use = v->peak;
     return FSP_OK;
 }
 
@@ -2062,6 +2143,7 @@ extern "C" fsp_status fsp_server_destroy(fsp_server *v) {
     }
     v->cv.notify_all();
     if (v->worker.joinable()) v->worker.join();
+    if (v->builder.joinable()) v->builder.join();  // finishes the build in progress, if any
     cudaSetDevice(v->device);
     const cudaError_t e = cudaDeviceSynchronize();
     for (auto &sl : v->slots) {
@@ -2070,7 +2152,9 @@ extern "C" fsp_status fsp_server_destroy(fsp_server *v) {
         cudaEventDestroy(sl.ev);
     }
     for (auto &w : v->idle_ws) cudaFree(w.W1), cudaFree(w.W2);
-    for (auto &kv : v->specs) fsp_plan_destroy(kv.second.plan);
+    for (auto &kv : v->specs)
+        if (kv.second.plan) fsp_plan_destroy(kv.second.plan);
+    cudaStreamDestroy(v->build_stream);
     v->magic = 0;
     delete v;
     return cuda_status(e);

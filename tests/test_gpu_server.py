@@ -87,3 +87,44 @@ def test_request_larger_than_budget_fails_cleanly(fsp):
     r2, f2 = _req(8, 0)  # small requests still go through
     assert srv.wait(srv.submit(r2, f2)) > 0
     srv.close()
+
+
+def test_small_request_completes_while_a_spectrum_is_built(fsp):
+    """A cold N = 256 Vico-Greengard (DCT route) request starts a spectrum build
+    of about 100 ms on the builder thread; a warm N = 32 request submitted just
+    after it is admitted and finished meanwhile, within a few ms, and the
+    budget (spectra + workspaces + the build's reserved temporaries) holds."""
+    import torch
+    budget = 6 << 30
+    srv = fsp.Server(budget_bytes=budget, max_slots=4)
+    small, fs = _req(32, 5)
+    srv.wait(srv.submit(small, fs, L=1.0, algo="he"))  # its spectrum is now cached
+    big, fb = _req(256, 6)
+    t_big = srv.submit(big, fb, L=1.0, algo="vg_dct")
+    t_small = srv.submit(small, torch.full_like(fs, float("nan")), L=1.0, algo="he")
+    lat_small = srv.wait(t_small)
+    st = srv.stats()
+    big_state = srv.poll(t_big)[0]
+    lat_big = srv.wait(t_big)
+    print("N=32 latency %.2f ms while the N=256 build ran (big state then %d), N=256 latency %.1f ms, "
+          "peak bytes %.3f GB" % (lat_small, big_state, lat_big, st["peak_bytes_in_use"] / 1e9))
+    assert big_state < srv.DONE and st["builds_in_flight"] >= 1  # the build was still going
+    assert lat_small < 20.0
+    assert lat_big > lat_small
+    assert srv.stats()["peak_bytes_in_use"] <= budget
+    ref = fsp.Plan(256, 1.0, "vg_dct", "f32").solve(big)
+    assert torch.equal(ref, fb)
+    srv.close()
+
+
+def test_vg_build_larger_than_budget_is_refused(fsp):
+    """FSP_VG builds its kernel on the (4N)^3 grid: at N = 128 that is 2.1 GB
+    of temporaries, refused under a 1 GB budget; the DCT route fits."""
+    srv = fsp.Server(budget_bytes=1 << 30, max_slots=2)
+    r, f = _req(128, 1)
+    with pytest.raises(fsp.FspError) as ei:
+        srv.wait(srv.submit(r, f, algo="vg"))
+    assert ei.value.status == fsp.FSP_ENOMEM
+    assert srv.wait(srv.submit(r, f, algo="vg_dct")) > 0
+    assert srv.stats()["peak_bytes_in_use"] <= 1 << 30
+    srv.close()

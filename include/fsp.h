@@ -66,7 +66,11 @@ typedef enum { FSP_HE = 0, FSP_VG = 1, FSP_VG_DCT = 2 } fsp_algo;
  * than its FP64 pipes; the spectrum is the FP64 one split into float pairs.
  * Only where the specialised kernels run: N = 32, 64, 128, 256, 512, or a
  * non-cubic box whose sizes are powers of two in that range
- * (FSP_EUNSUPPORTED otherwise); not in batches. */
+ * (FSP_EUNSUPPORTED otherwise); not in batches.  Double-float keeps FP32's
+ * exponent range: plan creation returns FSP_EUNSUPPORTED when the largest
+ * spectrum value lies outside [2^-80, 2^80] (that value is about
+ * 3e-6 L^2 (32/N)^3, so the box side L may range over about 1e-8 .. 1e14 at
+ * N = 32 .. 512), and the caller keeps 8 N^3 max|rho| below about 2^80. */
 typedef enum { FSP_F64 = 0, FSP_F32_MIXED = 1, FSP_F64_DF = 2 } fsp_dtype;
 
 typedef struct fsp_plan fsp_plan;
@@ -246,6 +250,20 @@ fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents)
  * the environment variable FSP_GENERIC_ONLY=1 before fsp_plan_create forces
  * the generic engine (used to test both paths on the same sizes). */
 int fsp_plan_uses_fast_path(const fsp_plan *plan);
+/* Bounds evidence without a sanitizer.  With FSP_CHECK_BOUNDS=1 in the
+ * environment at plan creation, every device buffer the plan allocates (the
+ * spectrum, workspaces, roots tables, staging buffers, the field's spectra and
+ * workspace, and the plan-time temporaries) is surrounded by 1 MB guard bands
+ * of one byte pattern.  fsp_plan_check_bounds synchronises the device and
+ * counts the guard bytes around the plan's live buffers that no longer hold
+ * the pattern (0 when every kernel stayed inside its buffers);
+ * FSP_EUNSUPPORTED for a plan created without the variable.
+ * fsp_bounds_freed_bad: such bytes found, process-wide, in guarded buffers
+ * when they were freed (temporaries at the end of plan creation, buffers of
+ * destroyed plans).  Nothing traps: the counts are read on the host. */
+fsp_status fsp_plan_check_bounds(const fsp_plan *plan, unsigned long long *bad_bytes);
+unsigned long long fsp_bounds_freed_bad(void);
+
 /* Kernel launches per fsp_solve: 3 when the fused plane passes serve the
  * plan (PA = pad + x-R2C + y-FFT of each z-plane in one thread-block
  * cluster, P3, PC = y-IFFT + x-C2R + crops; the plane's intermediate W1 goes

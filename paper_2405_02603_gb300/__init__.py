@@ -100,6 +100,10 @@ def lib(build_if_missing=True):
     L.fsp_host_alloc.restype = i
     L.fsp_host_free.argtypes = [vp, ctypes.c_size_t]
     L.fsp_host_free.restype = i
+    L.fsp_plan_check_bounds.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.fsp_plan_check_bounds.restype = i
+    L.fsp_bounds_freed_bad.argtypes = []
+    L.fsp_bounds_freed_bad.restype = ctypes.c_ulonglong
     L.fsp_plan_launches.argtypes = [vp]
     L.fsp_plan_launches.restype = i
     L.fsp_plan_set_wait_timeout.argtypes = [vp, d]
@@ -207,6 +211,13 @@ class Plan:
     def fast_path(self):
         """True when the specialised power-of-two kernels serve this plan."""
         return lib().fsp_plan_uses_fast_path(self._p) == 1
+
+    def check_bounds(self):
+        """Guard bytes changed around the plan's buffers (plans created with
+        FSP_CHECK_BOUNDS=1 in the environment)."""
+        bad = ctypes.c_ulonglong()
+        check(lib().fsp_plan_check_bounds(self._p, ctypes.byref(bad)), "fsp_plan_check_bounds")
+        return int(bad.value)
 
     @property
     def launches(self):

@@ -65,12 +65,131 @@ fsp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FSP_OK : FSP_E
     } while (0)
 
 // Device memory owned by one scope: freed on every exit path.
+// Bounds checking without a sanitizer (opt-in, FSP_CHECK_BOUNDS=1 in the
+// environment at plan creation): every device buffer the plan allocates --
+// spectrum, workspaces, tables, plan-time temporaries -- gets kGuard bytes of
+// the pattern kGuardByte on each side.  A kernel that stores outside its
+// buffer by less than that changes the pattern; fsp_plan_check_bounds counts
+// changed bytes around the plan's live buffers, and freeing a guarded buffer
+// (a temporary, or a destroyed plan's) adds its changed bytes to a process-
+// wide count.  Nothing traps: the counts are read on the host.
+constexpr size_t kGuard = 1 << 20;
+constexpr unsigned char kGuardByte = 0xA5;
+thread_local size_t t_guard = 0;  // guard of allocations made by this thread now
+std::mutex g_guard_mu;
+struct Guarded {
+    void *base;
+    size_t bytes;
+};
+std::map<const void *, Guarded> g_guarded;
+std::atomic<unsigned long long> g_guard_freed_bad{0};
+
+// max |x| over n doubles (the bit patterns of non-negative doubles order as
+// unsigned integers)
+__global__ void k_abs_max(const double *x, long long n, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(x[i])));
+    atomicMax(out, m);
+}
+
+fsp_status abs_max(const double *x, long long n, cudaStream_t s, double *out) {
+    unsigned long long *d = nullptr, h = 0;
+    if (cudaMalloc(&d, sizeof(*d)) != cudaSuccess) {
+        cudaGetLastError();
+        return FSP_ENOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(*d), s);
+    if (e == cudaSuccess) {
+        k_abs_max<<<256, 256, 0, s>>>(x, n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    std::memcpy(out, &h, sizeof(*out));
+    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}
+
+// Double-float keeps FP32's exponent range: a spectrum whose largest value is
+// outside [2^-80, 2^80] would lose the low words of its smaller entries to
+// underflow (or overflow outright), so such plans are refused.
+constexpr double kDfMinS = 0x1p-80, kDfMaxS = 0x1p80;
+
+bool bounds_check_requested() {
+    const char *e = std::getenv("FSP_CHECK_BOUNDS");
+    return e && e[0] == '1';
+}
+
+__global__ void k_count_not(const unsigned char *a, size_t n, unsigned char v, unsigned long long *out) {
+    unsigned long long c = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        c += a[i] != v;
+    if (c) atomicAdd(out, c);
+}
+
+// changed guard bytes around the guarded buffer at p (synchronous)
+unsigned long long guard_bad(const void *p, const Guarded &g) {
+    unsigned long long *d = nullptr, h = 0;
+    if (cudaMalloc(&d, sizeof(*d)) != cudaSuccess) return ~0ull;
+    cudaMemset(d, 0, sizeof(*d));
+    const unsigned char *base = static_cast<const unsigned char *>(g.base);
+    k_count_not<<<64, 256>>>(base, kGuard, kGuardByte, d);
+    k_count_not<<<64, 256>>>(base + kGuard + g.bytes, kGuard, kGuardByte, d);
+    cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    (void)p;
+    return h;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    Guarded g{nullptr, 0};
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        auto it = g_guarded.find(p);
+        if (it != g_guarded.end()) {
+            g = it->second;
+            g_guarded.erase(it);
+        }
+    }
+    if (!g.base) {
+        cudaFree(p);
+        return;
+    }
+    cudaDeviceSynchronize();
+    g_guard_freed_bad += guard_bad(p, g);
+    cudaFree(g.base);
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (!t_guard) return cudaMalloc(p, bytes);
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes + 2 * kGuard);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemset(base, kGuardByte, bytes + 2 * kGuard)) != cudaSuccess) {
+        cudaFree(base);
+        return e;
+    }
+    *p = static_cast<char *>(base) + kGuard;
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    g_guarded[*p] = Guarded{base, bytes};
+    return cudaSuccess;
+}
+
+// Allocations made while this object lives get guard bands when `on`.
+struct GuardScope {
+    size_t prev;
+    explicit GuardScope(bool on) : prev(t_guard) { t_guard = on ? kGuard : 0; }
+    ~GuardScope() { t_guard = prev; }
+};
+
 struct DevBuf {
     void *p = nullptr;
     ~DevBuf() {
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     }
-    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes); }
+    cudaError_t alloc(size_t bytes) { return dev_malloc(&p, bytes); }
     void *release() {
         void *q = p;
         p = nullptr;
@@ -394,6 +513,7 @@ struct fsp_plan {
     void *tw_y = nullptr, *tw_z = nullptr;
     cudaEvent_t ev[6] = {};
     bool timing = false;
+    bool guarded = false;  // FSP_CHECK_BOUNDS=1 at creation: buffers with guard bands
     size_t bytes = 0;
     double precompute_ms = 0;
 };
@@ -414,7 +534,7 @@ void plan_free(fsp_plan *p) {
     for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi, p->pipe_rho[0], p->pipe_rho[1],
                     p->pipe_phi[0], p->pipe_phi[1], p->SF[0], p->SF[1], p->SF[2], p->W3, p->tw_y, p->tw_z,
                     (void *)p->err})
-        if (q) cudaFree(q);
+        if (q) dev_free(q);
     for (cudaStream_t q : {p->pipe_h2d, p->pipe_d2h})
         if (q) cudaStreamDestroy(q);
     for (int i = 0; i < 2; ++i)
@@ -842,6 +962,8 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     const auto t0 = std::chrono::steady_clock::now();
 
     fsp_plan *p = new fsp_plan();
+    p->guarded = bounds_check_requested();
+    GuardScope guard_scope(p->guarded);
     p->N = N, p->L = L, p->h = L / N, p->algo = algo, p->dtype = dtype;
     p->rsize = dtype == FSP_F32_MIXED ? 4 : 8;  // caller's reals; a double-float is 8 bytes too
     p->P = ((N + 1) + 15) / 16 * 16;
@@ -914,6 +1036,12 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
         if ((st = enqueue_dct_spectrum(N, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
         const double hh = p->h;
         const double scale = hh * hh * hh / ((2.0 * N) * (2.0 * N) * (2.0 * N));
+        if (dtype == FSP_F64_DF) {
+            double mx = 0;
+            if ((st = abs_max((const double *)Td.p, (long long)(k1 * k1 * k1), s, &mx)) != FSP_OK) return fail(st);
+            mx *= std::fabs(scale);
+            if (!(mx >= kDfMinS && mx <= kDfMaxS)) return fail(FSP_EUNSUPPORTED);
+        }
         e = dtype == FSP_F64      ? launch_store_S<double>((double *)Td.p, p->S, N, p->P, scale, s)
             : dtype == FSP_F64_DF ? launch_store_S<df>((double *)Td.p, p->S, N, p->P, scale, s)
                                   : launch_store_S<float>((double *)Td.p, p->S, N, p->P, scale, s);
@@ -996,6 +1124,8 @@ fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();
     fsp_plan *p = new fsp_plan();
+    p->guarded = bounds_check_requested();
+    GuardScope guard_scope(p->guarded);
     p->aniso = true;
     p->fast = fast_ok;
     for (int a = 0; a < 3; ++a) p->n3[a] = nn[a], p->h3[a] = hh[a];
@@ -1058,6 +1188,12 @@ fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double 
         if ((st = enqueue_kernel_T3(nn, hh, algo, (double *)Td.p, s, tmp)) != FSP_OK) return fail(st);
         if ((st = enqueue_trig_spectrum3(nn, -1, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
         const double scale = hx * hy * hz / ((2.0 * nx) * (2.0 * ny) * (2.0 * nz));
+        if (dtype == FSP_F64_DF) {
+            double mx = 0;
+            if ((st = abs_max((const double *)Td.p, (long long)(nx + 1) * rows, s, &mx)) != FSP_OK) return fail(st);
+            mx *= std::fabs(scale);
+            if (!(mx >= kDfMinS && mx <= kDfMaxS)) return fail(FSP_EUNSUPPORTED);
+        }
         e = dtype == FSP_F64      ? launch_store_S3<double>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s)
             : dtype == FSP_F64_DF ? launch_store_S3<df>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s)
                                   : launch_store_S3<float>((double *)Td.p, p->S, nx + 1, rows, p->P, scale, s);
@@ -1095,6 +1231,7 @@ fsp_status fsp_plan_field_init(fsp_plan *plan, fsp_stream stream) {
     if (dev != plan->device) return FSP_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();
+    GuardScope guard_scope(plan->guarded);
     const int N = plan->N;
     // the box: cubic, or the plan's non-cubic sizes and spacings
     const int nn[3] = {plan->aniso ? plan->n3[0] : N, plan->aniso ? plan->n3[1] : N, plan->aniso ? plan->n3[2] : N};
@@ -1190,6 +1327,7 @@ fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void
     if (count == 0) return FSP_OK;
     const size_t bytes = plan_points(plan) * plan->rsize;
     if (!plan->pipe_h2d) {  // first use: staging pairs, copy streams, events
+        GuardScope guard_scope(plan->guarded);
         DevBuf a0, a1, b0, b1;
         fsp_status st;
         if ((st = alloc_or_nomem(a0, bytes)) != FSP_OK || (st = alloc_or_nomem(a1, bytes)) != FSP_OK ||
@@ -1299,6 +1437,34 @@ fsp_status fsp_plan_inject_stall(fsp_plan *plan) {
 }
 
 int fsp_plan_uses_fast_path(const fsp_plan *plan) { return plan_live(plan) ? (plan->fast ? 1 : 0) : -1; }
+
+fsp_status fsp_plan_check_bounds(const fsp_plan *plan, unsigned long long *bad_bytes) {
+    if (!plan_live(plan) || !bad_bytes) return FSP_EINVAL;
+    *bad_bytes = 0;
+    if (!plan->guarded) return FSP_EUNSUPPORTED;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FSP_ECUDA;
+    const fsp_plan *p = plan;
+    const void *bufs[] = {p->S,          p->W1,          p->W2,          p->tw_n,  p->tw_2n, p->stage_rho,
+                          p->stage_phi,  p->pipe_rho[0], p->pipe_rho[1], p->pipe_phi[0], p->pipe_phi[1],
+                          p->SF[0],      p->SF[1],       p->SF[2],       p->W3,    p->tw_y,  p->tw_z,
+                          (const void *)p->err};
+    for (const void *q : bufs) {
+        if (!q) continue;
+        Guarded g{nullptr, 0};
+        {
+            std::lock_guard<std::mutex> lk(g_guard_mu);
+            auto it = g_guarded.find(q);
+            if (it != g_guarded.end()) g = it->second;
+        }
+        if (!g.base) continue;
+        const unsigned long long b = guard_bad(q, g);
+        if (b == ~0ull) return FSP_ENOMEM;
+        *bad_bytes += b;
+    }
+    return FSP_OK;
+}
+
+unsigned long long fsp_bounds_freed_bad(void) { return g_guard_freed_bad.load(); }
 
 int fsp_plan_launches(const fsp_plan *plan) { return plan_live(plan) ? (plan->plane ? 3 : 5) : -1; }
 
@@ -1428,7 +1594,7 @@ void batch_free(fsp_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (void *q : {(void *)b->d_solves, (void *)b->d_segs, (void *)b->d_ctl})
-        if (q) cudaFree(q);
+        if (q) dev_free(q);
     b->magic = 0;
     delete b;
 }
@@ -1539,7 +1705,7 @@ fsp_status batch_build(fsp_batch *b, cudaStream_t s) {
         }
     b->total = first;
     for (void *q : {(void *)b->d_solves, (void *)b->d_segs, (void *)b->d_ctl})
-        if (q) cudaFree(q);
+        if (q) dev_free(q);
     b->d_solves = nullptr, b->d_segs = nullptr, b->d_ctl = nullptr;
     b->ctl_bytes = sizeof(BatchCtl) + sizeof(int) * (5 * (size_t)count);
     DevBuf ds, dg, dc;

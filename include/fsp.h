@@ -338,6 +338,12 @@ fsp_status fsp_batch_launch(fsp_batch *batch, fsp_stream stream);
 fsp_status fsp_batch_wait(fsp_batch *batch, fsp_stream stream);
 /* Change the per-wait time limit (milliseconds, > 0); rebuilds the graph. */
 fsp_status fsp_batch_set_timeout(fsp_batch *batch, double ms);
+/* The form a batch's graph takes (rebuilds the graph): 0 (default) the
+ * persistent kernel above; 1 the solves' own launches (each plan's
+ * fsp_solve kernels: the specialised ones for power-of-two N, else the
+ * generic engine) on 8 captured streams, a plan's solves on one stream, plans
+ * dealt round-robin.  Results are those of fsp_solve with each plan. */
+fsp_status fsp_batch_set_form(fsp_batch *batch, int form);
 /* Fault injection for tests, made on the host: one dependency of the work
  * list is raised by one tile that never exists, so that wait can only end by
  * its time limit.  Later launches then end with FSP_ETIMEOUT. */

@@ -114,6 +114,8 @@ def lib(build_if_missing=True):
     L.fsp_batch_wait.argtypes = [vp, vp]
     L.fsp_batch_set_timeout.argtypes = [vp, d]
     L.fsp_batch_inject_stall.argtypes = [vp]
+    L.fsp_batch_set_form.argtypes = [vp, i]
+    L.fsp_batch_set_form.restype = i
     L.fsp_batch_destroy.argtypes = [vp]
     L.fsp_solve_batched.argtypes = [vpp, vpp, vpp, i, vp]
     L.fsp_batch_autotune.argtypes = [vp, vp]
@@ -383,6 +385,10 @@ class Batch:
 
     def inject_stall(self):
         check(lib().fsp_batch_inject_stall(self._b), "fsp_batch_inject_stall")
+
+    def set_form(self, form):
+        """0: one persistent kernel; 1: the solves' own launches on 8 streams."""
+        check(lib().fsp_batch_set_form(self._b, int(form)), "fsp_batch_set_form")
 
     def close(self):
         if self._b is not None and self._b.value:

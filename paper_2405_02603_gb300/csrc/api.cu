@@ -1576,6 +1576,7 @@ struct fsp_batch {
     size_t ctl_bytes = 0;
     BatchLaunch launch{};
     double timeout_ms = 1000.0;
+    int form = 0;  // 0: one persistent kernel; 1: the solves' own launches on several streams
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -1642,15 +1643,48 @@ fsp_status batch_build_graph(fsp_batch *b) {
     b->launch.timeout_ns = (unsigned long long)(b->timeout_ms * 1e6);
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return FSP_ECUDA;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    // form 1: kStreams capture streams forked from cs; a plan's solves stay on
+    // one stream (they share its workspace), plans are dealt round-robin
+    constexpr int kStreams = 8;
+    cudaStream_t fs[kStreams] = {};
+    cudaEvent_t fev[kStreams + 1] = {};
+    cudaError_t e = cudaSuccess;
+    if (b->form == 1) {
+        for (int i = 0; i < kStreams && e == cudaSuccess; ++i)
+            e = cudaStreamCreateWithFlags(&fs[i], cudaStreamNonBlocking);
+        for (int i = 0; i <= kStreams && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&fev[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t e1 = cudaMemsetAsync(b->d_ctl, 0, b->ctl_bytes, cs);
-        cudaError_t e2 = e1 == cudaSuccess ? (b->dtype == FSP_F64 ? launch_batch_kernel<double>(b->launch, cs)
-                                                                  : launch_batch_kernel<float>(b->launch, cs))
-                                           : e1;
+        cudaError_t e2 = e1;
+        if (e1 == cudaSuccess && b->form == 0) {
+            e2 = b->dtype == FSP_F64 ? launch_batch_kernel<double>(b->launch, cs)
+                                     : launch_batch_kernel<float>(b->launch, cs);
+        } else if (e1 == cudaSuccess) {
+            e2 = cudaEventRecord(fev[kStreams], cs);
+            for (int i = 0; i < kStreams && e2 == cudaSuccess; ++i) e2 = cudaStreamWaitEvent(fs[i], fev[kStreams], 0);
+            std::map<const fsp_plan *, int> lane;
+            for (int i = 0; i < b->count && e2 == cudaSuccess; ++i) {
+                auto it = lane.find(b->plans[i]);
+                if (it == lane.end()) it = lane.emplace(b->plans[i], (int)lane.size() % kStreams).first;
+                const fsp_plan *p = b->plans[i];
+                e2 = enqueue_solve_ws(p, b->rho[i], b->phi[i], p->W1, p->W2, fs[it->second]);
+            }
+            for (int i = 0; i < kStreams && e2 == cudaSuccess; ++i) {
+                e2 = cudaEventRecord(fev[i], fs[i]);
+                if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, fev[i], 0);
+            }
+        }
         e = cudaStreamEndCapture(cs, &b->graph);
         if (e == cudaSuccess) e = e2;
     }
+    for (int i = 0; i < kStreams; ++i) {
+        if (fs[i]) cudaStreamDestroy(fs[i]);
+        if (fev[i]) cudaEventDestroy(fev[i]);
+    }
+    if (fev[kStreams]) cudaEventDestroy(fev[kStreams]);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     cudaStreamDestroy(cs);
     return cuda_status(e);
@@ -1782,6 +1816,15 @@ extern "C" fsp_status fsp_batch_wait(fsp_batch *b, fsp_stream stream) {
 extern "C" fsp_status fsp_batch_set_timeout(fsp_batch *b, double ms) {
     if (!batch_live(b) || !(ms > 0.0) || ms > 3.6e6) return FSP_EINVAL;
     b->timeout_ms = ms;
+    return batch_build_graph(b);
+}
+
+extern "C" fsp_status fsp_batch_set_form(fsp_batch *b, int form) {
+    if (!batch_live(b) || (form != 0 && form != 1)) return FSP_EINVAL;
+    if (form == 1)
+        for (const fsp_plan *p : b->plans)
+            if (!p->W1) return FSP_EINVAL;
+    b->form = form;
     return batch_build_graph(b);
 }
 

@@ -96,3 +96,29 @@ def test_batch_validation(fsp):
         fsp.Batch([p, p], [r, r], [torch.empty_like(r), torch.empty_like(r)])  # one workspace twice
     with pytest.raises(fsp.FspError):
         fsp.Batch([p, q], [r, r32], [torch.empty_like(r), torch.empty_like(r32)])  # mixed dtypes
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_graph_of_solves_form_bitwise_equals_single_solves(fsp, dtype):
+    """Form 1 replays the solves' own launches (specialised kernels for
+    power-of-two N, so plans here are the default ones), several per stream:
+    every result is bitwise that plan's fsp_solve."""
+    import torch
+    rng = np.random.default_rng(2406)
+    Ns = [int(x) for x in rng.choice(SIZES, size=20)]
+    plans = [fsp.Plan(N, 1.0, "vg_dct", dtype) for N in Ns]
+    rhos = [to_dev(I.gaussian_mixture(N, seed=3000 + i).astype(np.float32), dtype) for i, N in enumerate(Ns)]
+    phis = [torch.full_like(r, float("nan")) for r in rhos]
+    b = fsp.Batch(plans, rhos, phis)
+    b.set_form(1)
+    for rep in range(2):
+        b.launch()
+        assert b.wait() == fsp.FSP_OK
+        for p, r, f in zip(plans, rhos, phis):
+            assert torch.equal(p.solve(r), f)
+    b.set_form(0)  # back to the persistent kernel: still a valid batch
+    b.launch()
+    assert b.wait() == fsp.FSP_OK
+    b.close()
+    for p in plans:
+        p.close()

@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--no-systems", action="store_true", help="skip the batched and serving legs")
+    ap.add_argument("--summarize", default=None, choices=["traffic", "launches"],
+                    help="write the profiles/ summary of an ncu CSV (--ncu-csv): per-pass DRAM traffic of a "
+                         "--profile-case run (its stdout in --case-log), or the launch list of a bench run")
+    ap.add_argument("--ncu-csv", default=None)
+    ap.add_argument("--case-log", default=None)
+    ap.add_argument("--ncu-command", default="", help="the ncu command line, recorded in the summary")
     ap.add_argument("--profile-case", default=None, metavar="DTYPES",
                     help="small profiling case instead of the bench: for each dtype in the comma-separated list "
                          "(f32, f64, f64df; with a '-field' suffix, field solves) build an N-grid VG-DCT plan "
@@ -73,6 +79,7 @@ def profile_case(args):
     import torch
     import paper_2405_02603_gb300 as fsp
     N = args.n
+    cases = []
     for case in args.profile_case.split(","):
         dtype, field = case.split("-")[0], case.endswith("-field")
         plan = fsp.Plan(N, 1.0, "vg_dct", dtype)
@@ -82,8 +89,111 @@ def profile_case(args):
         for _ in range(2):
             plan.solve_field(rho) if field else plan.solve(rho)
         torch.cuda.synchronize()
+        # pass launches per solve: a field solve is the forward passes once,
+        # then P3 and the inverse passes per component
+        fwd, inv = (1, 1) if plan.launches == 3 else (2, 2)
+        cases.append([case, fwd + 3 * (1 + inv) if field else plan.launches])
         plan.close()
-    print(json.dumps({"profile_case": args.profile_case, "N": N, "ok": True}))
+    print(json.dumps({"profile_case": args.profile_case, "N": N, "ok": True, "launches_per_solve": cases}))
+
+
+PASS_KERNELS = ("k_fast_", "k_plane_", "k_p3_tma")  # the solve passes of the profile cases (N = 256)
+
+
+def read_ncu_csv(path):
+    """Launches of an ncu --csv log in order: [(name, {metric: value})]."""
+    import csv
+    rows = []
+    with open(path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    order, launches = [], {}
+    for r in csv.DictReader(lines):
+        key = r.get("ID")
+        if key not in launches:
+            launches[key] = (r["Kernel Name"], {})
+            order.append(key)
+        v = r.get("Metric Value", "").replace(",", "")
+        unit = r.get("Metric Unit", "").strip().lower()
+        scale = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "ns": 1e-3, "nsecond": 1e-3, "us": 1.0,
+                 "usecond": 1.0, "ms": 1e3, "msecond": 1e3, "s": 1e6, "second": 1e6}.get(unit, 1.0)  # bytes; us
+        try:
+            launches[key][1][r["Metric Name"]] = float(v) * scale
+        except ValueError:
+            pass
+    for k in order:
+        rows.append(launches[k])
+    return rows
+
+
+def summarize(args):
+    """profiles/ summaries from committed code only (see --summarize)."""
+    launches = read_ncu_csv(args.ncu_csv)
+    N = args.n
+    if args.summarize == "launches":
+        tot = {}
+        for name, m in launches:
+            t = m.get("gpu__time_duration.sum", 0.0)
+            c, us = tot.get(name, (0, 0.0))
+            tot[name] = (c + 1, us + t)
+        allus = sum(us for _, us in tot.values())
+        md = ["# Launch list of a bench run (N=%d)" % N, "",
+              "Command (one GB300, after the same command exited 0 without ncu): `%s`. ncu times are "
+              "serialised and cold: compare shares." % args.ncu_command, "",
+              "| kernel | launches | total us | share |", "|---|---|---|---|"]
+        for name, (c, us) in sorted(tot.items(), key=lambda kv: -kv[1][1]):
+            md.append("| `%s` | %d | %.1f | %.1f%% |" % (name.split("(")[0], c, us, 100 * us / allus))
+        solve = {n: v for n, v in tot.items() if any(k in n for k in PASS_KERNELS)}
+        sus = sum(us for _, us in solve.values())
+        md += ["", "## solve kernels only (their shares of the solve)", "",
+               "| kernel | launches | total us | share |", "|---|---|---|---|"]
+        for name, (c, us) in sorted(solve.items(), key=lambda kv: -kv[1][1]):
+            md.append("| `%s` | %d | %.1f | %.1f%% |" % (name.split("(")[0], c, us, 100 * us / sus))
+        with open(os.path.join(ROOT, "profiles", "bench_n%d_launch_list.md" % N), "w") as f:
+            f.write("\n".join(md) + "\n")
+        return
+    cases = None
+    with open(args.case_log) as f:
+        for ln in f:
+            if ln.startswith("{") and "launches_per_solve" in ln:
+                cases = json.loads(ln)["launches_per_solve"]
+    passes = [(n, m) for n, m in launches if any(k in n for k in PASS_KERNELS)]
+    out = {"kernel_src_sha": kernel_src_sha(), "kernel_sources": KERNEL_SOURCES,
+           "workload": "N=%d VG-DCT solve of the seeded 8-Gaussian mixture, second of two solves, per case" % N,
+           "command": args.ncu_command}
+    md = ["# Solve passes at N=%d: DRAM traffic per launch (ncu)" % N, "",
+          "Command (one GB300, after the same command exited 0 without ncu): `%s`; summarised by "
+          "`python bench.py --summarize traffic --ncu-csv <csv> --case-log <stdout of the plain run>`. Each case "
+          "builds an N=%d VG-DCT plan and runs two solves; the second solve's launches are listed. ncu times are "
+          "serialised and cold: compare shares." % (args.ncu_command, N), "",
+          "Kernel sources hash (sha256 of %s, first 16 hex): `%s`; bench.py reports `roofline.traffic` from the "
+          "JSON beside this file only while the sources still hash to this value." % (", ".join(KERNEL_SOURCES),
+                                                                                    out["kernel_src_sha"])]
+    i = 0
+    for case, k in cases:
+        second = passes[i + k:i + 2 * k]
+        i += 2 * k
+        key = case.replace("-", "_")
+        c, r = (8, 4) if case.startswith("f32") else (16, 8)
+        alg = field_bytes(N, c, r) if "field" in case else sum(pass_bytes(N, c, r))
+        out[key] = {"per_launch_bytes": [m.get("dram__bytes_read.sum", 0) + m.get("dram__bytes_write.sum", 0)
+                                         for _, m in second],
+                    "scale_to_full": 1.0, "kernels": [n for n, _ in second]}
+        md += ["", "## %s" % case, "", "| launch | kernel | DRAM read MB | DRAM write MB | ncu time us |",
+               "|---|---|---|---|---|"]
+        for j, (n, m) in enumerate(second):
+            t = m.get("gpu__time_duration.sum", 0.0)
+            md.append("| %d | `%s` | %.1f | %.1f | %.1f |" % (
+                j + 1, n.split("(")[0], m.get("dram__bytes_read.sum", 0) / 1e6, m.get("dram__bytes_write.sum", 0) / 1e6,
+                t))
+        tot = sum(out[key]["per_launch_bytes"])
+        md.append("")
+        md.append("Total %.3f GB of DRAM traffic per %s; the byte model (bench.py) gives %.3f GB." % (
+            tot / 1e9, "field solve" if "field" in case else "solve", alg / 1e9))
+    base = os.path.join(ROOT, "profiles", "solve_n%d_dram_traffic" % N)
+    with open(base + ".json", "w") as f:
+        json.dump(out, f, indent=1)
+    with open(base + ".md", "w") as f:
+        f.write("\n".join(md) + "\n")
 
 
 def pass_bytes(N, c, r):
@@ -756,6 +866,9 @@ def main():
         return
     if args.profile_case:
         profile_case(args)
+        return
+    if args.summarize:
+        summarize(args)
         return
     import torch
     rank = int(os.environ.get("RANK", "0"))

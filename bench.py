@@ -981,8 +981,10 @@ def main():
             out["e_max_%s_n%d" % (d, N)] = out["e_max_vs_oracle"][d]
         for n in ("128", "512"):
             r = out["precision"].get(n, {}).get(d, {})
-            if "e_max_vs_oracle" in r or "e_max_vs_oracle_sampled" in r:
-                out["e_max_%s_n%s" % (d, n)] = r.get("e_max_vs_oracle", r.get("e_max_vs_oracle_sampled"))
+            if "e_max_vs_oracle" in r:
+                out["e_max_%s_n%s" % (d, n)] = r["e_max_vs_oracle"]
+            elif "e_max_vs_oracle_sampled" in r:
+                out["e_max_%s_n%s_sampled" % (d, n)] = r["e_max_vs_oracle_sampled"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

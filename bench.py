@@ -51,6 +51,9 @@ NSRC = 4
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--mode", default="solve", choices=["solve", "dist"],
+                    help="solve: the benchmark (replicas across ranks); dist: one slab-decomposed solve across "
+                         "the ranks (strong scaling, all-to-all over NCCL)")
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fsp", choices=["fsp", "reference"])
@@ -65,6 +68,7 @@ def parse():
     ap.add_argument("--ncu-csv", default=None)
     ap.add_argument("--case-log", default=None)
     ap.add_argument("--ncu-command", default="", help="the ncu command line, recorded in the summary")
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "profiles"), help="where --summarize writes")
     ap.add_argument("--profile-case", default=None, metavar="DTYPES",
                     help="small profiling case instead of the bench: for each dtype in the comma-separated list "
                          "(f32, f64, f64df; with a '-field' suffix, field solves) build an N-grid VG-DCT plan "
@@ -148,7 +152,7 @@ def summarize(args):
                "| kernel | launches | total us | share |", "|---|---|---|---|"]
         for name, (c, us) in sorted(solve.items(), key=lambda kv: -kv[1][1]):
             md.append("| `%s` | %d | %.1f | %.1f%% |" % (name.split("(")[0], c, us, 100 * us / sus))
-        with open(os.path.join(ROOT, "profiles", "bench_n%d_launch_list.md" % N), "w") as f:
+        with open(os.path.join(args.out_dir, "bench_n%d_launch_list.md" % N), "w") as f:
             f.write("\n".join(md) + "\n")
         return
     cases = None
@@ -189,7 +193,7 @@ def summarize(args):
         md.append("")
         md.append("Total %.3f GB of DRAM traffic per %s; the byte model (bench.py) gives %.3f GB." % (
             tot / 1e9, "field solve" if "field" in case else "solve", alg / 1e9))
-    base = os.path.join(ROOT, "profiles", "solve_n%d_dram_traffic" % N)
+    base = os.path.join(args.out_dir, "solve_n%d_dram_traffic" % N)
     with open(base + ".json", "w") as f:
         json.dump(out, f, indent=1)
     with open(base + ".md", "w") as f:
@@ -801,6 +805,61 @@ def precision_leg(fsp, Ns, L, W, world, with_oracle):
     return out
 
 
+def dist_bench(fsp, args, world, rank):
+    """One N^3 VG-DCT solve split over the ranks in slabs (fsp_dist_*): P1/P2
+    on z-slabs, all-to-all, P3/P4 on k_x slabs, all-to-all, P5; the exchange
+    over torch.distributed (NCCL) point-to-point, or device copies for one
+    rank.  K timed solves between barriers, the max over ranks; each rank's
+    slab of phi compared with its own single-GPU solve of the whole grid."""
+    import torch
+    N, L, K, W = args.n, 1.0, args.steps, max(3, args.warmup)
+    p = fsp.DistPlan(N, L, "vg_dct", "f32", world, rank)
+    full = I.gaussian_mixture(N).astype(np.float32)
+    rho = torch.from_numpy(full[p.z0:p.z1].copy()).cuda()
+    phi = torch.empty_like(rho)
+    s0, r0, s1, r1 = p.blocks(0, True), p.blocks(0, False), p.blocks(1, True), p.blocks(1, False)
+
+    def exchange(snd, rcv):
+        if world > 1:
+            fsp.exchange_dist(snd, rcv)
+        else:
+            fsp.exchange_local([snd], [rcv])
+
+    def step():
+        p.forward(rho, s0)
+        exchange(s0, r0)
+        p.middle(r0, s1)
+        exchange(s1, r1)
+        p.backward(r1, phi)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(K):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    tmax = max_over_ranks(t0.elapsed_time(t1), world)
+    one = fsp.Plan(N, L, "vg_dct", "f32")
+    ref = one.solve(torch.from_numpy(full).cuda())[p.z0:p.z1]
+    err = float((phi.double() - ref.double()).abs().max() / ref.double().abs().max())
+    one.close()
+    err = max_over_ranks(err, world)
+    p.close()
+    return {"metric": "slab-decomposed VG-DCT solves/s at N=%d across the ranks (strong scaling)" % N,
+            "mode": "dist", "value": round(K / (tmax * 1e-3), 2), "unit": "solves/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": round(tmax / K, 4), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded 8-Gaussian mixture (seed 2405), float32-rounded",
+            "config": {"workload": "one N=%d^3 solve in z/k_x slabs, two all-to-alls per solve" % N, "N": N,
+                       "L": L, "algo": "vg_dct", "parallelism": "slabs%d" % world},
+            "e_max_vs_single_gpu": err}
+
+
 def bench_config(N, L, algo, world):
     """The workload's config object, the same in both arms of the bench."""
     return {"workload": "VG free-space solve (Sec. 2.2 steps 1-5, Vico-Greengard spectrum), N=%d^3 "
@@ -886,6 +945,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2405_02603_gb300 as fsp
     fsp.lib()
+    if args.mode == "dist":
+        out = dist_bench(fsp, args, world, rank)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     N, L, K, W = args.n, 1.0, args.steps, max(3, args.warmup)
     hbm, hbm_kind = measured_peaks()
 

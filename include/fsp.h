@@ -243,9 +243,10 @@ fsp_status fsp_plan_destroy(fsp_plan *plan);
  */
 fsp_status fsp_plan_set_timing(fsp_plan *plan, void *const *events, int nevents);
 
-/* 1 when this plan's solves run the specialised power-of-two kernels (N = 32,
- * 64, 128, 256, 512, or a non-cubic box of such sizes; compile-time radix
- * schedules, register-resident), 0 when they run the generic mixed-radix
+/* 1 when this plan's solves run the specialised kernels (N = 32, 64, 128,
+ * 256, 512, or a non-cubic box of such sizes; FSP_F64 and FSP_F32_MIXED also
+ * N = 48, 96, 192; compile-time radix schedules, register-resident), 0 when
+ * they run the generic mixed-radix
  * engine, -1 for an invalid plan.  Setting
  * the environment variable FSP_GENERIC_ONLY=1 before fsp_plan_create forces
  * the generic engine (used to test both paths on the same sizes). */

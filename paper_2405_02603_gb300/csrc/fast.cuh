@@ -195,11 +195,41 @@ template <typename T, int D> struct RD {
             for (int k2 = 0; k2 < (HO ? B / 2 : B); ++k2) v[k1 + 4 * k2] = h[k2];
         }
     }
+    // Radix 3: X1, X2 = a - (b + c)/2 +- i D (sqrt 3 / 2)(b - c).  Never a
+    // padded first or a cropped last stage (those stay even).
+    template <bool HZ, bool HO> static __device__ __forceinline__ void d3(C *v) {
+        static_assert(!HZ && !HO, "radix 3 runs only as a middle stage");
+        constexpr T s3 = T(D * 0.86602540378443864676372317075294);
+        const C a = v[0], t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        const C u = C{a.x - T(0.5) * t.x, a.y - T(0.5) * t.y};
+        const C w = C{-s3 * d.y, s3 * d.x};
+        v[0] = cadd(a, t);
+        v[1] = cadd(u, w);
+        v[2] = csub(u, w);
+    }
+    // Radix 6 = 2 x 3: E = DFT3 of the even inputs, O of the odd ones,
+    // X[q] = E[q] + w6^q O[q], X[q+3] = E[q] - w6^q O[q], w6 = exp(D 2 pi i / 6).
+    template <bool HZ, bool HO> static __device__ __forceinline__ void d6(C *v) {
+        static_assert(!HZ && !HO, "radix 6 runs only as a middle stage");
+        constexpr T s3 = T(D * 0.86602540378443864676372317075294);
+        C e[3] = {v[0], v[2], v[4]}, o[3] = {v[1], v[3], v[5]};
+        d3<false, false>(e);
+        d3<false, false>(o);
+        const C o1 = C{T(0.5) * o[1].x - s3 * o[1].y, s3 * o[1].x + T(0.5) * o[1].y};    // w6 o1
+        const C o2 = C{-T(0.5) * o[2].x - s3 * o[2].y, s3 * o[2].x - T(0.5) * o[2].y};   // w6^2 o2
+        v[0] = cadd(e[0], o[0]), v[3] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1), v[4] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2), v[5] = csub(e[2], o2);
+    }
     template <int R, bool HZ, bool HO> static __device__ __forceinline__ void dft(C *v) {
         if constexpr (R == 2)
             d2<HZ, HO>(v);
+        else if constexpr (R == 3)
+            d3<HZ, HO>(v);
         else if constexpr (R == 4)
             d4<HZ, HO>(v);
+        else if constexpr (R == 6)
+            d6<HZ, HO>(v);
         else if constexpr (R == 8)
             d8<HZ, HO>(v);
         else
@@ -650,6 +680,12 @@ template <typename T, int n> struct Cfg {
         static constexpr int V = VV, L = LL, R1 = A, R2 = B, R3 = CC;      \
     };
 FSP_CFG(float, 32, 8, 16, 4, 8, 1)
+// 3 * 2^k: the odd radix as the middle stage (the first and last stay even
+// for the padded loads and the cropped stores)
+FSP_CFG(float, 48, 12, 16, 4, 3, 4)
+FSP_CFG(float, 96, 24, 16, 4, 3, 8)
+FSP_CFG(float, 192, 24, 16, 8, 3, 8)
+FSP_CFG(float, 384, 24, 16, 8, 6, 8)
 FSP_CFG(float, 64, 8, 16, 8, 8, 1)
 FSP_CFG(float, 128, 16, 16, 8, 16, 1)
 FSP_CFG(float, 256, 16, 16, 16, 16, 1)
@@ -657,6 +693,10 @@ FSP_CFG(float, 512, 32, 16, 16, 32, 1)
 FSP_CFG(float, 1024, 16, 16, 16, 16, 4)
 FSP_CFG(float, 2048, 16, 8, 16, 16, 8)  // column passes of non-cubic boxes only (an axis of 1024)
 FSP_CFG(double, 32, 8, 16, 4, 8, 1)
+FSP_CFG(double, 48, 12, 8, 4, 3, 4)
+FSP_CFG(double, 96, 24, 8, 4, 3, 8)
+FSP_CFG(double, 192, 24, 8, 8, 3, 8)
+FSP_CFG(double, 384, 24, 8, 8, 6, 8)
 FSP_CFG(double, 64, 8, 16, 8, 8, 1)
 FSP_CFG(double, 128, 16, 8, 8, 16, 1)
 FSP_CFG(double, 256, 16, 8, 16, 16, 1)
@@ -766,6 +806,9 @@ template <typename T, int N, bool R2C> cudaError_t launch_row_n(const RowArgs &a
 
 template <typename T, int MODE> cudaError_t launch_col(int n, const ColArgs &a, int nbatch, cudaStream_t s) {
     switch (n) {
+    case 96: return launch_col_n<T, 96, MODE>(a, nbatch, s);
+    case 192: return launch_col_n<T, 192, MODE>(a, nbatch, s);
+    case 384: return launch_col_n<T, 384, MODE>(a, nbatch, s);
     case 64: return launch_col_n<T, 64, MODE>(a, nbatch, s);
     case 128: return launch_col_n<T, 128, MODE>(a, nbatch, s);
     case 256: return launch_col_n<T, 256, MODE>(a, nbatch, s);
@@ -777,6 +820,9 @@ template <typename T, int MODE> cudaError_t launch_col(int n, const ColArgs &a, 
 
 template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, cudaStream_t s) {
     switch (N) {
+    case 48: return launch_row_n<T, 48, R2C>(a, s);
+    case 96: return launch_row_n<T, 96, R2C>(a, s);
+    case 192: return launch_row_n<T, 192, R2C>(a, s);
     case 32: return launch_row_n<T, 32, R2C>(a, s);
     case 64: return launch_row_n<T, 64, R2C>(a, s);
     case 128: return launch_row_n<T, 128, R2C>(a, s);
@@ -787,7 +833,11 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
 }
 
 #define FSP_FAST_INSTANTIATE(T)                                                                                \
-    template <> bool has<T>(int N) { return N == 32 || N == 64 || N == 128 || N == 256 || N == 512; }           \
+    template <> bool has<T>(int N) {                                                                           \
+        return N == 32 || N == 64 || N == 128 || N == 256 || N == 512 ||                                      \
+               (N == 48 && Cfg<T, 48>::Ok && Cfg<T, 96>::Ok) || (N == 96 && Cfg<T, 96>::Ok && Cfg<T, 192>::Ok) || \
+               (N == 192 && Cfg<T, 192>::Ok && Cfg<T, 384>::Ok);                                               \
+    }                                                                                                          \
     template <> cudaError_t p1<T>(int N, const RowArgs &a, cudaStream_t s) { return launch_row<T, true>(N, a, s); } \
     template <> cudaError_t p5<T>(int N, const RowArgs &a, cudaStream_t s) { return launch_row<T, false>(N, a, s); } \
     template <> cudaError_t p2<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \

@@ -1,4 +1,6 @@
-"""The specialised power-of-two kernels (N = 32..512) against the generic
+"""The specialised kernels (power-of-two N = 32..512, and N = 48, 96, 192,
+whose line lengths 3 * 2^k put a radix-3 or radix-6 stage in the middle of
+the schedule) against the generic
 mixed-radix engine on the same plans' inputs, and against the oracle at
 N = 128; the environment switch FSP_GENERIC_ONLY=1 selects the generic engine
 at plan creation."""
@@ -25,8 +27,10 @@ def _plan(fsp, N, algo, dtype, generic):
             os.environ["FSP_GENERIC_ONLY"] = old
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("N", [32, 64, 128, 256, 512])
+FAST = {"f64": [32, 48, 64, 96, 128, 192, 256, 512], "f32": [32, 48, 64, 96, 128, 192, 256, 512]}
+
+
+@pytest.mark.parametrize("dtype,N", [(d, n) for d in ("f64", "f32") for n in FAST[d]])
 def test_fast_equals_generic(fsp, N, dtype):
     pf = _plan(fsp, N, "vg_dct", dtype, generic=False)
     pg = _plan(fsp, N, "vg_dct", dtype, generic=True)

@@ -544,8 +544,9 @@ def batch_leg(fsp, dtype, count=64, launches=5):
     out.update(res[0])
     out["form"] = "one persistent kernel per launch over all 64 solves, CUDA graph replay"
     out["tiles"] = "generic-engine tile shapes from the autotuned table paper_2405_02603_gb300/tuning/gb300.txt"
-    out["graph_of_solves"] = dict(res[1], form="one CUDA graph of the 64 solves' own launches (specialised "
-                                               "kernels for N = 32, 64, 128) on 8 streams")
+    out["graph_of_solves"] = dict(res[1], form="one CUDA graph of the 64 solves' own launches (the "
+                                               "specialised kernels of every size in FP32; FP64: all but "
+                                               "N = 160) on 8 streams")
     return out
 
 

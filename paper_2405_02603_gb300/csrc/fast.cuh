@@ -207,6 +207,25 @@ template <typename T, int D> struct RD {
         v[1] = cadd(u, w);
         v[2] = csub(u, w);
     }
+    // Radix 5: with t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4, t4 = v2 - v3,
+    // X1,4 = v0 + c1 t1 + c2 t2 +- i D (s1 t3 + s2 t4), X2,3 = v0 + c2 t1 +
+    // c1 t2 +- i D (s2 t3 - s1 t4); c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5).
+    template <bool HZ, bool HO> static __device__ __forceinline__ void d5(C *v) {
+        static_assert(!HZ && !HO, "radix 5 runs only as a middle stage");
+        constexpr T c1 = T(0.30901699437494742410229341718282), c2 = T(-0.80901699437494742410229341718282);
+        constexpr T s1 = T(D * 0.95105651629515357211643933337938), s2 = T(D * 0.58778525229247312916870595463907);
+        const C v0 = v[0], t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]),
+                t4 = csub(v[2], v[3]);
+        const C m1 = C{v0.x + c1 * t1.x + c2 * t2.x, v0.y + c1 * t1.y + c2 * t2.y};
+        const C m2 = C{v0.x + c2 * t1.x + c1 * t2.x, v0.y + c2 * t1.y + c1 * t2.y};
+        const C n1 = C{s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y};
+        const C n2 = C{s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y};
+        v[0] = C{v0.x + t1.x + t2.x, v0.y + t1.y + t2.y};
+        v[1] = C{m1.x - n1.y, m1.y + n1.x};
+        v[4] = C{m1.x + n1.y, m1.y - n1.x};
+        v[2] = C{m2.x - n2.y, m2.y + n2.x};
+        v[3] = C{m2.x + n2.y, m2.y - n2.x};
+    }
     // Radix 6 = 2 x 3: E = DFT3 of the even inputs, O of the odd ones,
     // X[q] = E[q] + w6^q O[q], X[q+3] = E[q] - w6^q O[q], w6 = exp(D 2 pi i / 6).
     template <bool HZ, bool HO> static __device__ __forceinline__ void d6(C *v) {
@@ -228,6 +247,8 @@ template <typename T, int D> struct RD {
             d3<HZ, HO>(v);
         else if constexpr (R == 4)
             d4<HZ, HO>(v);
+        else if constexpr (R == 5)
+            d5<HZ, HO>(v);
         else if constexpr (R == 6)
             d6<HZ, HO>(v);
         else if constexpr (R == 8)
@@ -686,6 +707,9 @@ FSP_CFG(float, 48, 12, 16, 4, 3, 4)
 FSP_CFG(float, 96, 24, 16, 4, 3, 8)
 FSP_CFG(float, 192, 24, 16, 8, 3, 8)
 FSP_CFG(float, 384, 24, 16, 8, 6, 8)
+// 5 * 2^k (N = 160): radix 5 in the middle
+FSP_CFG(float, 160, 40, 16, 4, 5, 8)
+FSP_CFG(float, 320, 40, 16, 8, 5, 8)
 FSP_CFG(float, 64, 8, 16, 8, 8, 1)
 FSP_CFG(float, 128, 16, 16, 8, 16, 1)
 FSP_CFG(float, 256, 16, 16, 16, 16, 1)
@@ -809,6 +833,7 @@ template <typename T, int MODE> cudaError_t launch_col(int n, const ColArgs &a, 
     case 96: return launch_col_n<T, 96, MODE>(a, nbatch, s);
     case 192: return launch_col_n<T, 192, MODE>(a, nbatch, s);
     case 384: return launch_col_n<T, 384, MODE>(a, nbatch, s);
+    case 320: return launch_col_n<T, 320, MODE>(a, nbatch, s);
     case 64: return launch_col_n<T, 64, MODE>(a, nbatch, s);
     case 128: return launch_col_n<T, 128, MODE>(a, nbatch, s);
     case 256: return launch_col_n<T, 256, MODE>(a, nbatch, s);
@@ -823,6 +848,7 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
     case 48: return launch_row_n<T, 48, R2C>(a, s);
     case 96: return launch_row_n<T, 96, R2C>(a, s);
     case 192: return launch_row_n<T, 192, R2C>(a, s);
+    case 160: return launch_row_n<T, 160, R2C>(a, s);
     case 32: return launch_row_n<T, 32, R2C>(a, s);
     case 64: return launch_row_n<T, 64, R2C>(a, s);
     case 128: return launch_row_n<T, 128, R2C>(a, s);
@@ -836,7 +862,7 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
     template <> bool has<T>(int N) {                                                                           \
         return N == 32 || N == 64 || N == 128 || N == 256 || N == 512 ||                                      \
                (N == 48 && Cfg<T, 48>::Ok && Cfg<T, 96>::Ok) || (N == 96 && Cfg<T, 96>::Ok && Cfg<T, 192>::Ok) || \
-               (N == 192 && Cfg<T, 192>::Ok && Cfg<T, 384>::Ok);                                               \
+               (N == 192 && Cfg<T, 192>::Ok && Cfg<T, 384>::Ok) || (N == 160 && Cfg<T, 160>::Ok && Cfg<T, 320>::Ok); \
     }                                                                                                          \
     template <> cudaError_t p1<T>(int N, const RowArgs &a, cudaStream_t s) { return launch_row<T, true>(N, a, s); } \
     template <> cudaError_t p5<T>(int N, const RowArgs &a, cudaStream_t s) { return launch_row<T, false>(N, a, s); } \

@@ -27,7 +27,7 @@ def _plan(fsp, N, algo, dtype, generic):
             os.environ["FSP_GENERIC_ONLY"] = old
 
 
-FAST = {"f64": [32, 48, 64, 96, 128, 192, 256, 512], "f32": [32, 48, 64, 96, 128, 192, 256, 512]}
+FAST = {"f64": [32, 48, 64, 96, 128, 192, 256, 512], "f32": [32, 48, 64, 96, 128, 160, 192, 256, 512]}
 
 
 @pytest.mark.parametrize("dtype,N", [(d, n) for d in ("f64", "f32") for n in FAST[d]])

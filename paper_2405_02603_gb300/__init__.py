@@ -656,12 +656,15 @@ def exchange_dist(sends, recvs, group=None):
     import torch.distributed as dist
     me, R = dist.get_rank(group), dist.get_world_size(group)
     real = lambda t: torch.view_as_real(t) if t.is_complex() else t  # noqa: E731
-    works = []
+    ops = []
     for q in range(R):
         if q == me:
             recvs[q].copy_(sends[q])
             continue
-        works.append(dist.isend(real(sends[q]).contiguous(), q, group=group))
-        works.append(dist.irecv(real(recvs[q]), q, group=group))
-    for w in works:
-        w.wait()
+        ops.append(dist.P2POp(dist.isend, real(sends[q]).contiguous(), q, group=group))
+        ops.append(dist.P2POp(dist.irecv, real(recvs[q]), q, group=group))
+    # posted as one group: separate NCCL sends and receives would each wait
+    # for a peer whose matching call is queued behind its own send
+    if ops:
+        for w in dist.batch_isend_irecv(ops):
+            w.wait()

@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <unordered_set>
 
 #include "../../include/fsp.h"
 #include "internal.h"
@@ -37,6 +39,9 @@ using namespace fsp;
 namespace {
 
 constexpr uint64_t kDistMagic = 0x46535044'49535431ULL;  // "FSPDIST1"
+// live handles: a destroyed or foreign pointer is refused without reading it
+std::mutex g_dist_mu;
+std::unordered_set<const void *> g_dists;
 
 // dst[a dA + b dB + c] = src[a sA + b sB + c], (a, b, c) < (A, B, C); one
 // complex value per thread, c fastest (coalesced on both sides)
@@ -79,6 +84,8 @@ struct fsp_dist {
     size_t csize = 0;
     void *W1 = nullptr, *W2 = nullptr, *V = nullptr, *U = nullptr;
 };
+
+static void dist_free(fsp_dist *d);
 
 extern "C" {
 
@@ -135,11 +142,15 @@ fsp_status fsp_dist_create(fsp_dist **out, int N, double L, fsp_algo algo, fsp_d
     for (int i = 0; i < 4; ++i) {
         if (cudaMalloc(bufs[i], sizes[i] ? sizes[i] : 16) != cudaSuccess) {
             cudaGetLastError();
-            fsp_dist_destroy(d);
+            dist_free(d);
             return FSP_ENOMEM;
         }
     }
     d->magic = kDistMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_dist_mu);
+        g_dists.insert(d);
+    }
     *out = d;
     return FSP_OK;
 }
@@ -148,7 +159,10 @@ fsp_status fsp_dist_create(fsp_dist **out, int N, double L, fsp_algo algo, fsp_d
 
 namespace {
 
-bool dist_live(const fsp_dist *d) { return d && d->magic == kDistMagic; }
+bool dist_live(const fsp_dist *d) {
+    std::lock_guard<std::mutex> lk(g_dist_mu);
+    return d && g_dists.count(d) && d->magic == kDistMagic;
+}
 
 template <typename T> cudaError_t dist_forward(fsp_dist *d, const void *rho, void *const *send, cudaStream_t s) {
     const internal::PlanView &v = d->pv;
@@ -278,14 +292,21 @@ fsp_status fsp_dist_backward(fsp_dist *d, const void *const *recv, void *phi_sla
 }
 
 fsp_status fsp_dist_destroy(fsp_dist *d) {
-    if (!d) return FSP_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(g_dist_mu);
+        if (!d || !g_dists.erase(d)) return FSP_EINVAL;
+    }
+    dist_free(d);
+    return FSP_OK;
+}
+
+}  // extern "C"
+
+static void dist_free(fsp_dist *d) {
     cudaDeviceSynchronize();
     for (void *q : {d->W1, d->W2, d->V, d->U})
         if (q) cudaFree(q);
     if (d->spec) fsp_plan_destroy(d->spec);
     d->magic = 0;
     delete d;
-    return FSP_OK;
 }
-
-}  // extern "C"

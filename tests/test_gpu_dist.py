@@ -52,4 +52,7 @@ def test_dist_rejects_bad_arguments(fsp):
     arr = (ctypes.c_void_p * 2)(blocks[0].data_ptr(), None)
     rho = to_dev(np.zeros((4, 8, 8)), "f64")
     assert lib.fsp_dist_forward(p._d, ctypes.c_void_p(rho.data_ptr()), arr, None) == fsp.FSP_EINVAL
+    stale = ctypes.c_void_p(p._d.value)
     p.close()
+    assert lib.fsp_dist_destroy(stale) == fsp.FSP_EINVAL  # destroyed: refused without reading it
+    assert lib.fsp_dist_middle(stale, arr, arr, None) == fsp.FSP_EINVAL

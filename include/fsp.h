@@ -292,6 +292,28 @@ double fsp_plan_precompute_ms(const fsp_plan *plan);
 fsp_status fsp_plan_spectrum(const fsp_plan *plan, double *s_host);
 
 /*
+ * fsp_plan_create_from_spectrum -- a cubic plan whose multiplier is a stored
+ * one: s_host holds the (N+1)^3 doubles fsp_plan_spectrum wrote for a plan of
+ * the same N and L (same layout, already scaled by h^3 / (2N)^3), so the
+ * plan-time precompute of Sec. 2.2-2.4 (for FSP_VG a DFT of the (4N)^3
+ * grid) is replaced by one host-to-device copy.  Checkpoint and warm start:
+ * a restarted job or server restores its plans without recomputing them.
+ * The values are stored as given, rounded to the plan's dtype (a fresh plan
+ * rounds its FP64 spectrum the same way), so the spectrum of an FSP_F64 plan
+ * restores a plan of any dtype to exactly the multiplier a fresh plan of that
+ * dtype holds, and one of an FSP_F32_MIXED plan restores an FSP_F32_MIXED
+ * plan bit for bit (FP32 values are exact doubles).
+ * N, L and algo are checked as in fsp_plan_create; nothing checks that
+ * s_host belongs to that (N, L, algo).
+ * s_host is read during the call only (the caller keeps it).  FSP_EINVAL for
+ * a null pointer or a non-finite value, otherwise the statuses of
+ * fsp_plan_create (for FSP_F64_DF also the range check of its spectrum).
+ * Synchronous on stream.
+ */
+fsp_status fsp_plan_create_from_spectrum(fsp_plan **out, int N, double L, fsp_algo algo, fsp_dtype dtype,
+                                         const double *s_host, fsp_stream stream);
+
+/*
  * fsp_kernel_T -- the real-space kernel T[m], m in [0,N]^3, of `algo`
  * (Sec. 2.2 step 3, Sec. 2.3, Sec. 2.4), computed on the current device in
  * FP64 exactly as fsp_plan_create computes it, written to the DEVICE array

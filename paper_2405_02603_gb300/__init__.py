@@ -72,6 +72,7 @@ def lib(build_if_missing=True):
     L.fsp_plan_precompute_ms.argtypes = [vp]
     L.fsp_plan_precompute_ms.restype = d
     L.fsp_plan_spectrum.argtypes = [vp, vp]
+    L.fsp_plan_create_from_spectrum.argtypes = [ctypes.POINTER(vp), i, d, i, i, vp, vp]
     L.fsp_kernel_T.argtypes = [i, d, i, vp, vp]
     L.fsp_fft_c2c.argtypes = [i, i, i, i, vp, vp, vp]
     L.fsp_plan_set_timing.argtypes = [vp, ctypes.POINTER(vp), i]
@@ -171,6 +172,9 @@ def _algo_code(algo):
 def torch_dtype(dtype):
     import torch
     return torch.float32 if _dtype_code(dtype) == 1 else torch.float64
+
+
+SPECTRUM_FORMAT = "fsp-spectrum-1"  # the .npz layout of Plan.save
 
 
 class Plan:
@@ -284,6 +288,49 @@ class Plan:
         out = np.empty(tuple(d + 1 for d in self.shape), dtype=np.float64)
         check(lib().fsp_plan_spectrum(self._p, ctypes.c_void_p(out.ctypes.data)), "fsp_plan_spectrum")
         return out
+
+    @classmethod
+    def from_spectrum(cls, N, L, algo, dtype, S, stream=None):
+        """A cubic plan whose multiplier is the stored spectrum S ((N+1)^3
+        doubles, as spectrum() returns them): fsp_plan_create_from_spectrum,
+        one copy instead of the plan-time precompute."""
+        import numpy as np
+        N, L = int(N), float(L)
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        if S.shape != (N + 1,) * 3:
+            raise FspError(FSP_EINVAL, "spectrum must have shape %s, got %s" % ((N + 1,) * 3, S.shape))
+        self = cls.__new__(cls)
+        self.algo, self.dtype = algo, dtype
+        self._p = ctypes.c_void_p()
+        self.N, self.L, self.h = N, L, L / N
+        self.n3, self.h3, self.L3 = (N,) * 3, (self.h,) * 3, (L,) * 3
+        self.shape = (N,) * 3
+        self.npoints = N ** 3
+        check(lib().fsp_plan_create_from_spectrum(ctypes.byref(self._p), N, L, _algo_code(algo), _dtype_code(dtype),
+                                                  ctypes.c_void_p(S.ctypes.data), _stream_handle(stream)),
+              "fsp_plan_create_from_spectrum")
+        return self
+
+    def save(self, path):
+        """Write the plan's (N, L, algo, dtype) and spectrum to a .npz file
+        (cubic plans), for Plan.load to restore without the precompute."""
+        import numpy as np
+        if self.n3 != (self.N,) * 3 or self.L3 != (self.L,) * 3:
+            raise FspError(FSP_EUNSUPPORTED, "save: cubic plans only")
+        name = lambda table, v: next(k for k, c in table.items() if c == table.get(v, v))  # noqa: E731
+        np.savez(path, format=np.array(SPECTRUM_FORMAT), N=np.int64(self.N), L=np.float64(self.L),
+                 algo=np.array(name(ALGOS, self.algo)), dtype=np.array(name(DTYPES, self.dtype)), S=self.spectrum())
+
+    @classmethod
+    def load(cls, path, dtype=None, stream=None):
+        """The plan a file of Plan.save describes, in its dtype or in `dtype`
+        (an FP64 spectrum restores any dtype exactly as a fresh plan)."""
+        import numpy as np
+        with np.load(path, allow_pickle=False) as z:
+            if str(z["format"]) != SPECTRUM_FORMAT:
+                raise FspError(FSP_EINVAL, "not a spectrum file of this format: %r" % str(z["format"]))
+            return cls.from_spectrum(int(z["N"]), float(z["L"]), str(z["algo"]),
+                                     str(z["dtype"]) if dtype is None else dtype, z["S"], stream)
 
     def set_timing(self, events):
         """Record the 6 torch.cuda.Event objects around the 5 passes of each

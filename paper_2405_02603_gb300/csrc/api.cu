@@ -949,8 +949,10 @@ const char *fsp_status_str(fsp_status s) {
 }  // extern "C"
 
 namespace {
+// s_host: null to compute the spectrum (Sec. 2.2-2.4), else (N+1)^3 doubles
+// of a stored one (the octant fsp_plan_spectrum writes, already scaled)
 fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo algo, fsp_dtype dtype,
-                            fsp_stream stream, bool with_workspace) {
+                            fsp_stream stream, bool with_workspace, const double *s_host = nullptr) {
     if (!out) return FSP_EINVAL;
     *out = nullptr;
     fsp_status st = validate_size(N, L, algo);
@@ -1032,10 +1034,17 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
         Temps tmp, tw;
         DevBuf Td;
         if ((st = alloc_or_nomem(Td, sizeof(double) * k1 * k1 * k1)) != FSP_OK) return fail(st);
-        if ((st = enqueue_kernel_T(N, L, algo, (double *)Td.p, s, tmp)) != FSP_OK) return fail(st);
-        if ((st = enqueue_dct_spectrum(N, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
         const double hh = p->h;
-        const double scale = hh * hh * hh / ((2.0 * N) * (2.0 * N) * (2.0 * N));
+        double scale = hh * hh * hh / ((2.0 * N) * (2.0 * N) * (2.0 * N));
+        if (s_host) {  // a stored spectrum: upload it as it is
+            if (cudaMemcpyAsync(Td.p, s_host, sizeof(double) * k1 * k1 * k1, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
+                return fail(FSP_ECUDA);
+            scale = 1.0;
+        } else {
+            if ((st = enqueue_kernel_T(N, L, algo, (double *)Td.p, s, tmp)) != FSP_OK) return fail(st);
+            if ((st = enqueue_dct_spectrum(N, (double *)Td.p, s, tw)) != FSP_OK) return fail(st);
+        }
         if (dtype == FSP_F64_DF) {
             double mx = 0;
             if ((st = abs_max((const double *)Td.p, (long long)(k1 * k1 * k1), s, &mx)) != FSP_OK) return fail(st);
@@ -1081,6 +1090,19 @@ extern "C" {
 fsp_status fsp_plan_create(fsp_plan **out, int N, double L, double h, fsp_algo algo, fsp_dtype dtype,
                            fsp_stream stream) {
     return plan_create_impl(out, N, L, h, algo, dtype, stream, true);
+}
+
+fsp_status fsp_plan_create_from_spectrum(fsp_plan **out, int N, double L, fsp_algo algo, fsp_dtype dtype,
+                                         const double *s_host, fsp_stream stream) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    if (!s_host) return FSP_EINVAL;
+    if (N >= 2 && N <= kMaxN) {  // every value finite (a truncated or corrupt file shows here first)
+        const size_t tot = (size_t)(N + 1) * (N + 1) * (N + 1);
+        for (size_t i = 0; i < tot; ++i)
+            if (!std::isfinite(s_host[i])) return FSP_EINVAL;
+    }
+    return plan_create_impl(out, N, L, L / N, algo, dtype, stream, true, s_host);
 }
 
 fsp_status fsp_plan_create_aniso(fsp_plan **out, int nx, int ny, int nz, double hx, double hy, double hz,

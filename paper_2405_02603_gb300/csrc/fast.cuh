@@ -126,6 +126,22 @@ template <typename T, int D> struct RD {
         }
     }
 
+    // t + rot(d) and t - rot(d).  FP32 writes them per component (the sign
+    // folds into the scalar adds), so only the plain complex sums take the
+    // packed two-float form; the other types use the complex helpers.
+    static __device__ __forceinline__ C addrot(C t, C d) {
+        if constexpr (std::is_same<T, float>::value)
+            return D < 0 ? C{t.x + d.y, t.y - d.x} : C{t.x - d.y, t.y + d.x};
+        else
+            return cadd(t, rot(d));
+    }
+    static __device__ __forceinline__ C subrot(C t, C d) {
+        if constexpr (std::is_same<T, float>::value)
+            return D < 0 ? C{t.x - d.y, t.y + d.x} : C{t.x + d.y, t.y - d.x};
+        else
+            return csub(t, rot(d));
+    }
+
     template <bool HZ, bool HO> static __device__ __forceinline__ void d2(C *v) {
         if constexpr (HZ) {
             v[1] = v[0];
@@ -136,18 +152,18 @@ template <typename T, int D> struct RD {
         }
     }
     template <bool HZ, bool HO> static __device__ __forceinline__ void d4(C *v) {
-        C t0, t1, t2, t3;
+        C t0, t1, t2, d;  // outputs 1 and 3 are t1 +- rot(d)
         if constexpr (HZ) {
-            t0 = v[0], t1 = v[0], t2 = v[1], t3 = rot(v[1]);
+            t0 = v[0], t1 = v[0], t2 = v[1], d = v[1];
         } else {
             t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-            t2 = cadd(v[1], v[3]), t3 = rot(csub(v[1], v[3]));
+            t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
         }
         v[0] = cadd(t0, t2);
-        v[1] = cadd(t1, t3);
+        v[1] = addrot(t1, d);
         if constexpr (!HO) {
             v[2] = csub(t0, t2);
-            v[3] = csub(t1, t3);
+            v[3] = subrot(t1, d);
         }
     }
     template <bool HZ, bool HO> static __device__ __forceinline__ void d8(C *v) {
@@ -157,13 +173,12 @@ template <typename T, int D> struct RD {
         d4<HZ, false>(e);
         d4<HZ, false>(o);
         o[1] = w32<4>(o[1]);
-        o[2] = w32<8>(o[2]);
-        o[3] = w32<12>(o[3]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = cadd(e[q], o[q]);
+        o[3] = w32<12>(o[3]);  // o[2] takes w32<8> = rot in addrot / subrot
+        v[0] = cadd(e[0], o[0]), v[1] = cadd(e[1], o[1]);
+        v[2] = addrot(e[2], o[2]), v[3] = cadd(e[3], o[3]);
         if constexpr (!HO) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q + 4] = csub(e[q], o[q]);
+            v[4] = csub(e[0], o[0]), v[5] = csub(e[1], o[1]);
+            v[6] = subrot(e[2], o[2]), v[7] = csub(e[3], o[3]);
         }
     }
     // R = 4 B (B = 4 or 8): x[B n1 + n2] -> DFT_4 over n1 per n2, twiddle
@@ -375,6 +390,9 @@ template <typename T, int MODE, int n> struct ColOpt {
     static constexpr bool DF = std::is_same<T, df>::value;
     static constexpr bool F32 = std::is_same<T, float>::value;
     static constexpr bool PF = ZL && !DF;
+    // CTAs per SM the register allocation must allow (2: k_fast_col_occ2):
+    // two 256-thread tiles of the FP32 P3 on lines of 512 (N = 256)
+    static constexpr int MINB = ZL && F32 && n == 512 ? 2 : 1;
     static constexpr bool TWS = (DF && MODE != COL_INV) || (MODE == COL_FMO && !std::is_same<T, double>::value) ||
                                 (MODE == COL_FMI && F32 && n == 1024);
 };
@@ -382,8 +400,8 @@ template <typename T, int MODE, int n> struct ColOpt {
 // RG (a non-cubic box): the strides, the number of lines (k_x <= n_x) and the
 // fold of the batch index (k_y <= n_y) come from the arguments instead of
 // ColGeo; the cube keeps its compile-time geometry.
-template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG = false>
-__global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
+template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG>
+__device__ __forceinline__ void fast_col_body(const ColArgs &a) {
     using C = cx_t<T>;
     using G = ColGeo<n, MODE>;
     constexpr int TPL = n / V, N = G::N;
@@ -539,6 +557,25 @@ __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
             });
         });
     }
+}
+
+// The column kernels: the plain launch bound leaves the register count to
+// the compiler; k_fast_col_occ2 caps it so that two CTAs fit on an SM
+// (ColOpt::MINB), where the compiler would otherwise take a few more.
+template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG = false>
+__global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
+    fast_col_body<T, n, V, L, R1, R2, R3, MODE, RG>(a);
+}
+template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG = false>
+__global__ void __launch_bounds__(L *(n / V), 2) k_fast_col_occ2(const ColArgs a) {
+    fast_col_body<T, n, V, L, R1, R2, R3, MODE, RG>(a);
+}
+template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG>
+constexpr auto col_kernel() {
+    if constexpr (ColOpt<T, MODE, n>::MINB == 2)
+        return k_fast_col_occ2<T, n, V, L, R1, R2, R3, MODE, RG>;
+    else
+        return k_fast_col<T, n, V, L, R1, R2, R3, MODE, RG>;
 }
 
 // ------------------------------------------------------- row kernels --
@@ -765,7 +802,7 @@ template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a
     if constexpr (!K::Ok) {
         return cudaErrorInvalidValue;
     } else {
-        auto kern = k_fast_col<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE>;
+        auto kern = col_kernel<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE, false>();
         const size_t sm = sizeof(cx_t<T>) * n * (K::L + 1) + (ColOpt<T, MODE, n>::TWS ? sizeof(cx_t<T>) * n : 0);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -786,7 +823,7 @@ template <typename T, int n, int MODE> cudaError_t launch_col_rg_n(const ColArgs
     if constexpr (!K::Ok) {
         return cudaErrorInvalidValue;
     } else {
-        auto kern = k_fast_col<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE, true>;
+        auto kern = col_kernel<T, n, K::V, K::L, K::R1, K::R2, K::R3, MODE, true>();
         const int nx = a.nlines - 1;
         if (nx <= 0 || nx % K::L != 0 || nbatch % K::L != 0) return cudaErrorInvalidValue;
         ColArgs b = a;

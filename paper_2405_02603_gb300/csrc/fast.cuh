@@ -726,6 +726,171 @@ __global__ void __launch_bounds__(L *(N / V)) k_fast_c2r(const RowArgs a) {
     }
 }
 
+// ------------------------------------ row kernels, one lane per position --
+// FP32 rows with a two-stage schedule whose last radix is V (N = 32 .. 512):
+// the TPL threads of a row are consecutive lanes, so position p = t + TPL c of
+// the row is register c of lane t.  The first stage's inputs and the last
+// stage's outputs then move between registers and global memory directly
+// (TPL lanes cover TPL consecutive complex values), and the one exchange
+// between the stages uses a row-major shared buffer with one pad slot per
+// TPL positions, free of bank conflicts for both of its access patterns.
+// Both pair Z[p] (P1) or X[p] (P5) with the value at N - p by a warp
+// shuffle: lane TPL - t, register V-1-c (lane 0: its own register (V-c) mod V,
+// and X[N] for p = 0 in P5).
+template <typename T, int N, int V, int R1, int R2, int R3> struct LaneRow {
+    static constexpr int TPL = N / V;
+    static constexpr bool ok = std::is_same<T, float>::value && R3 == 1 && R2 == V && V % R1 == 0 &&
+                               TPL >= 4 && 32 % TPL == 0;
+    // row stride: room for positions 0..N (N + N/TPL + 1 slots), rounded up to
+    // TPL mod 16, so that the rows of one half-warp start on distinct banks
+    static constexpr int LDT = (N + V + 1) + ((TPL - (N + V + 1)) % 16 + 16) % 16;
+    static __device__ __forceinline__ int idx(int pos, int l) { return l * LDT + pos + pos / TPL; }
+};
+// CTAs per SM for the launch bound, from a register target per thread: 64
+// at N = 128, 256 (measured: P5 at N = 256 0.044 ms with 64 registers
+// against 0.047 with the compiler's 72), 48 at N = 64 and 64 at N = 32 (what
+// the compiler takes there by itself), 128 at N = 512 (two 256-thread CTAs)
+template <int N, int V, int L> constexpr int lane_row_minb() {
+    return 65536 / (L * (N / V) * (N == 64 ? 48 : N <= 256 ? 64 : 128));
+}
+template <typename T, int N, int V, int L> constexpr size_t lane_row_smem() {
+    return (size_t)L * LaneRow<T, N, V, 1, V, 1>::LDT * sizeof(cx_t<T>);
+}
+
+// the exchange between the two stages: stage-0 outputs of butterfly
+// b = t + k TPL at b R1 + r, stage-1 inputs at t + r TPL
+template <typename T, int D, int N, int V, int L, int R1>
+__device__ __forceinline__ void lane_row_stages(cx_t<T> *v, cx_t<T> *buf, int t, int l, const cx_t<T> *tw,
+                                                bool hz, bool ho) {
+    using X = LaneRow<T, N, V, R1, V, 1>;
+    using S = Stg<T, D, N, V, L>;
+    constexpr int TPL = N / V;
+    if (hz)
+        S::template compute<R1, 1, true, false>(v, t, tw);
+    else
+        S::template compute<R1, 1, false, false>(v, t, tw);
+#pragma unroll
+    for (int k = 0; k < V / R1; ++k)
+#pragma unroll
+        for (int r = 0; r < R1; ++r) buf[X::idx((t + k * TPL) * R1 + r, l)] = v[k * R1 + r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = buf[X::idx(t + r * TPL, l)];
+    if (ho)
+        S::template compute<V, R1, false, true>(v, t, tw);
+    else
+        S::template compute<V, R1, false, false>(v, t, tw);
+}
+
+// P1, lane per position: same arithmetic as k_fast_r2c
+template <typename T, int N, int V, int L, int R1>
+__global__ void __launch_bounds__(L *(N / V), (lane_row_minb<N, V, L>())) k_lane_r2c(const RowArgs a) {
+    using C = cx_t<T>;
+    constexpr int TPL = N / V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
+    const long long row = (long long)blockIdx.x * L + l;
+    const bool live = row < a.nrows;
+    using R = typename io_of<T>::t;
+    const R *xr = reinterpret_cast<const R *>(a.x) + (live ? row : 0) * N;
+    const C *tw = reinterpret_cast<const C *>(a.tw);
+    C v[V];
+    // stage 0 (zero upper half): z[m] = (x[2m], x[2m+1]) at m = t + k TPL + r N/R1 < N/2
+#pragma unroll
+    for (int k = 0; k < V / R1; ++k)
+#pragma unroll
+        for (int r = 0; r < R1 / 2; ++r)
+            v[k * R1 + r] = live ? load_pair<T>(xr, t + k * TPL + r * (N / R1)) : C{T(0), T(0)};
+    lane_row_stages<T, -1, N, V, L, R1>(v, buf, t, l, tw, true, false);
+    // v[c] = Z[t + c TPL].  X[q] = E + w^q O, X[N-q] = conj(E - w^q O) for
+    // q <= N/2, E, O from (Z[q], Z[N-q]); each lane computes its own positions
+    const C *tw2 = reinterpret_cast<const C *>(a.tw2);
+    C *crow = reinterpret_cast<C *>(a.c) + (live ? row : 0) * row_pitch(N);
+    const int lane = tid & 31, src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        C zp;  // Z[N - p], p = t + c TPL
+        zp.x = __shfl_sync(0xffffffffu, v[V - 1 - c].x, src);
+        zp.y = __shfl_sync(0xffffffffu, v[V - 1 - c].y, src);
+        if (t == 0) zp = v[(V - c) % V];
+        const int p = t + c * TPL;
+        const bool lo = c < V / 2 || p == N / 2;  // p <= N/2
+        const C zk = lo ? v[c] : zp, zc = lo ? zp : v[c];
+        const C e = C{T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
+        const C o = C{T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
+        if (p == 0) {
+            if (live) {
+                crow[0] = cadd(e, o);
+                crow[N] = csub(e, o);
+            }
+        } else {
+            const C wo = cmul(ldg_c(tw2 + (lo ? p : N - p)), o);
+            if (live) crow[p] = lo ? cadd(e, wo) : cconj(csub(e, wo));
+        }
+    }
+}
+
+// P5, lane per position: same arithmetic as k_fast_c2r
+template <typename T, int N, int V, int L, int R1>
+__global__ void __launch_bounds__(L *(N / V), (lane_row_minb<N, V, L>())) k_lane_c2r(const RowArgs a) {
+    using C = cx_t<T>;
+    constexpr int TPL = N / V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int tid = threadIdx.x, t = tid % TPL, l = tid / TPL;
+    const long long row = (long long)blockIdx.x * L + l;
+    const bool live = row < a.nrows;
+    const C *crow = reinterpret_cast<const C *>(a.c) + (live ? row : 0) * row_pitch(N);
+    C x[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) x[c] = live ? crow[t + c * TPL] : C{T(0), T(0)};
+    const C xn = live && t == 0 ? crow[N] : C{T(0), T(0)};
+    // Z[q] = A + i conj(w^q) B, Z[N-q] = conj A + i w^q conj B for q <= N/2,
+    // A, B from (X[q], X[N-q]).  Positions t + c TPL and t + (V-1-c) TPL are
+    // done together: their partners are registers V-1-c and c of lane TPL - t
+    // (lane 0: X[N] or its own register V - c, and its register c + 1), so each
+    // coefficient is last read in the iteration that consumes it.  Z[t + c TPL]
+    // goes to stage 0's register (c mod (V/R1)) R1 + c / (V/R1) (its position
+    // t + k TPL + r N/R1).
+    const C *tw2 = reinterpret_cast<const C *>(a.tw2);
+    const int lane = tid & 31, src = (lane & ~(TPL - 1)) | ((TPL - t) & (TPL - 1));
+    C v[V];
+    auto zof = [&](int c, C xc_own, C xp) {
+        const int p = t + c * TPL;
+        const bool lo = c < V / 2 || p == N / 2;
+        const C xk = lo ? xc_own : xp, xc = lo ? xp : xc_own;
+        const C A = C{xk.x + xc.x, xk.y - xc.y};
+        const C B = C{xk.x - xc.x, xk.y + xc.y};
+        const C w = ldg_c(tw2 + (lo ? p : N - p));
+        v[(c % (V / R1)) * R1 + c / (V / R1)] =
+            lo ? cadd(A, cmuli(cmul(cconj(w), B))) : cadd(cconj(A), cmuli(cmul(w, cconj(B))));
+    };
+#pragma unroll
+    for (int c = 0; c < V / 2; ++c) {
+        const int cc = V - 1 - c;
+        C p0, p1;  // partners of positions t + c TPL and t + cc TPL
+        p0.x = __shfl_sync(0xffffffffu, x[cc].x, src);
+        p0.y = __shfl_sync(0xffffffffu, x[cc].y, src);
+        p1.x = __shfl_sync(0xffffffffu, x[c].x, src);
+        p1.y = __shfl_sync(0xffffffffu, x[c].y, src);
+        if (t == 0) {
+            p0 = c == 0 ? xn : x[V - c];
+            p1 = x[c + 1];
+        }
+        zof(c, x[c], p0);
+        zof(cc, x[cc], p1);
+    }
+    lane_row_stages<T, +1, N, V, L, R1>(v, buf, t, l, reinterpret_cast<const C *>(a.tw), false, true);
+    // the first N/2 positions t + c TPL (c < V/2) hold z[m] = (x[2m], x[2m+1])
+    using R = typename io_of<T>::t;
+    R *xr = reinterpret_cast<R *>(const_cast<void *>(a.x)) + (live ? row : 0) * N;
+    if (live) {
+#pragma unroll
+        for (int c = 0; c < V / 2; ++c) store_pair<T>(xr, t + c * TPL, v[c]);
+    }
+}
+
 // ----------------------------------------------------- configurations --
 // Tile shape and radix schedule per (type, length); Ok = false: no fast path.
 template <typename T, int n> struct Cfg {
@@ -855,9 +1020,17 @@ template <typename T, int N, bool R2C> cudaError_t launch_row_n(const RowArgs &a
     if constexpr (!K::Ok) {
         return cudaErrorInvalidValue;
     } else {
-        auto kern = R2C ? k_fast_r2c<T, N, K::V, K::L, K::R1, K::R2, K::R3>
-                        : k_fast_c2r<T, N, K::V, K::L, K::R1, K::R2, K::R3>;
-        const size_t sm = smem_for<T, N>(N + 1);
+        constexpr bool lane = LaneRow<T, N, K::V, K::R1, K::R2, K::R3>::ok;
+        void (*kern)(const RowArgs);
+        size_t sm;
+        if constexpr (lane) {
+            kern = R2C ? k_lane_r2c<T, N, K::V, K::L, K::R1> : k_lane_c2r<T, N, K::V, K::L, K::R1>;
+            sm = lane_row_smem<T, N, K::V, K::L>();
+        } else {
+            kern = R2C ? k_fast_r2c<T, N, K::V, K::L, K::R1, K::R2, K::R3>
+                       : k_fast_c2r<T, N, K::V, K::L, K::R1, K::R2, K::R3>;
+            sm = smem_for<T, N>(N + 1);
+        }
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)((a.nrows + K::L - 1) / K::L), K::L * (N / K::V), sm, s>>>(a);

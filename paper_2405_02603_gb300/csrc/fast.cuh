@@ -950,6 +950,10 @@ template <> struct ColCfg<float, 512, COL_INV> {
     static constexpr bool Ok = true;
     static constexpr int V = 16, L = 16, R1 = 16, R2 = 16, R3 = 2;
 };
+template <> struct ColCfg<float, 512, COL_FWD> {
+    static constexpr bool Ok = true;
+    static constexpr int V = 16, L = 16, R1 = 16, R2 = 16, R3 = 2;
+};
 
 template <typename T, int n> constexpr size_t smem_for(int positions) {
     return (size_t)positions * (Cfg<T, n>::L + 1) * sizeof(cx_t<T>);

@@ -1013,10 +1013,12 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     if (with_workspace && (st = alloc_or_nomem(bW1, w1)) != FSP_OK) return fail(st);
     if (with_workspace && (st = alloc_or_nomem(bW2, w2)) != FSP_OK) return fail(st);
     if ((st = alloc_or_nomem(bt1, csize * N)) != FSP_OK) return fail(st);
-    if ((st = alloc_or_nomem(bt2, csize * 2 * N)) != FSP_OK) return fail(st);
+    // the cubic FP32 P3's stage twiddle tables follow the 2N roots
+    const int tt_len = p->fast && dtype == FSP_F32_MIXED ? fast::p3_table_len<float>(N) : 0;
+    if ((st = alloc_or_nomem(bt2, csize * (2 * N + tt_len))) != FSP_OK) return fail(st);
     p->S = bS.release(), p->W1 = bW1.release(), p->W2 = bW2.release();
     p->tw_n = bt1.release(), p->tw_2n = bt2.release();
-    p->bytes = sbytes + (with_workspace ? w1 + w2 : 0) + csize * 3 * N;
+    p->bytes = sbytes + (with_workspace ? w1 + w2 : 0) + csize * (3 * N + tt_len);
     cudaError_t e;
     if (dtype == FSP_F64) {
         e = launch_roots<double>(p->tw_n, N, s);
@@ -1027,6 +1029,7 @@ fsp_status plan_create_impl(fsp_plan **out, int N, double L, double h, fsp_algo 
     } else {
         e = launch_roots<float>(p->tw_n, N, s);
         if (e == cudaSuccess) e = launch_roots<float>(p->tw_2n, 2 * N, s);
+        if (e == cudaSuccess && tt_len) e = fast::p3_table_fill<float>(N, p->tw_2n, s);
     }
     if (e != cudaSuccess) return fail(FSP_ECUDA);
 

@@ -309,6 +309,27 @@ template <typename T, int D, int n, int V, int L, bool TWS = false> struct Stg {
         });
     }
 
+    // compute with this stage's table tt[j R + r] = w_n^(r j n/(Ns R)) (the
+    // same roots as twid reads; r = 0 unused); FP32 only (pairs as float4)
+    template <int R, int Ns, bool HZ, bool HO>
+    static __device__ __forceinline__ void compute_tt(C *v, int t, const C *__restrict__ tt) {
+        static_assert(std::is_same<T, float>::value && R % 2 == 0 && Ns > 1, "FP32 twiddled stages only");
+        StaticFor<0, V / R>::run([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            const unsigned j = (unsigned)(t + k * TPL) % (unsigned)Ns;
+            const float4 *row = reinterpret_cast<const float4 *>(tt + j * R);
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) {
+                const float4 w2 = __ldg(row + q);
+                C w0 = C{w2.x, w2.y}, w1 = C{w2.z, w2.w};
+                if (D > 0) w0.y = -w0.y, w1.y = -w1.y;
+                if (q > 0) v[k * R + 2 * q] = cmul(v[k * R + 2 * q], w0);
+                v[k * R + 2 * q + 1] = cmul(v[k * R + 2 * q + 1], w1);
+            }
+            RD<T, D>::template dft<R, HZ, HO>(v + k * R);
+        });
+    }
+
     template <int R> static __device__ __forceinline__ void load_in(C *v, const C *buf, int t, int l) {
 #pragma unroll
         for (int k = 0; k < V / R; ++k)
@@ -393,6 +414,10 @@ template <typename T, int MODE, int n> struct ColOpt {
     // CTAs per SM the register allocation must allow (2: k_fast_col_occ2):
     // two 256-thread tiles of the FP32 P3 on lines of 512 (N = 256)
     static constexpr int MINB = ZL && F32 && n == 512 ? 2 : 1;
+    // TT: the twiddled stages of the cubic P3 read per-stage tables [j][r]
+    // (after the n roots; see p3_table_fill): a pair of twiddles per 16-byte
+    // load at an immediate offset, no index arithmetic per twiddle
+    static constexpr bool TT = MODE == COL_FMI && F32 && n == 512;
     static constexpr bool TWS = (DF && MODE != COL_INV) || (MODE == COL_FMO && !std::is_same<T, double>::value) ||
                                 (MODE == COL_FMI && F32 && n == 1024);
 };
@@ -483,8 +508,19 @@ __device__ __forceinline__ void fast_col_body(const ColArgs &a) {
             });
         });
     }
+    // per-stage twiddle tables after the n roots: the forward's second stage
+    // (radix R2 over Ns = R1) at tw + n, the inverse's (R1 over R2) at tw + 2n
+    constexpr bool TT = O::TT && !RG && R3 == 1;
     Stg<T, D0, n, V, L, O::TWS>::template compute<R1, 1, HZ0, false>(v, t, tw);
-    run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV, O::TWS>(v, buf, t, l, tw, false);
+    if constexpr (TT) {
+        using SF = Stg<T, D0, n, V, L>;
+        SF::template store_out<R1, 1>(buf, v, t, l);
+        __syncthreads();
+        SF::template load_in<R2>(v, buf, t, l);
+        SF::template compute_tt<R2, R1, false, false>(v, t, tw + n);
+    } else {
+        run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV, O::TWS>(v, buf, t, l, tw, false);
+    }
 
     if constexpr (G::ZL) {
         // multiply by the real, even spectrum at the folded frequency
@@ -535,7 +571,15 @@ __device__ __forceinline__ void fast_col_body(const ColArgs &a) {
             run_rest<T, +1, n, V, L, R3, R2, R1, true, O::TWS>(v, buf, t, l, tw, true);
         } else {
             SI::template compute<R2, 1, false, false>(v, t, tw);
-            run_rest<T, +1, n, V, L, R2, R1, 1, true, O::TWS>(v, buf, t, l, tw, true);
+            if constexpr (TT) {
+                __syncthreads();
+                SI::template store_out<R2, 1>(buf, v, t, l);
+                __syncthreads();
+                SI::template load_in<R1>(v, buf, t, l);
+                SI::template compute_tt<R1, R2, false, true>(v, t, tw + 2 * n);
+            } else {
+                run_rest<T, +1, n, V, L, R2, R1, 1, true, O::TWS>(v, buf, t, l, tw, true);
+            }
         }
         constexpr int RF = R1;  // last radix of the reversed schedule
         StaticFor<0, V / RF>::run([&](auto kc) {
@@ -966,6 +1010,37 @@ template <typename T, int n> constexpr size_t smem_for(int positions) {
 namespace fsp {
 namespace fast {
 
+// The per-stage tables of the cubic P3 (ColOpt::TT), gathered from the n
+// roots tw[e] = w_n^e so that they hold exactly the values the other
+// kernels read: forward stage (radix R2 over Ns = R1) [j][r] = tw[r j n/(R1
+// R2)] for j < R1, r < R2, then the inverse's (radix R1 over Ns = R2) [j][r]
+// for j < R2, r < R1.
+template <typename T, int n, int R1, int R2> __global__ void k_p3_table(cx_t<T> *tw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * n) return;
+    constexpr int tws = n / (R1 * R2);
+    const int fwd = i < n, ii = fwd ? i : i - n, R = fwd ? R2 : R1;
+    const int j = ii / R, r = ii % R;
+    tw[n + i] = tw[r * j * tws];
+}
+template <typename T, int n> constexpr int p3_table_len_n() {
+    using K = ColCfg<T, n, COL_FMI>;
+    if constexpr (!K::Ok)
+        return 0;
+    else
+        return ColOpt<T, COL_FMI, n>::TT && K::R3 == 1 ? 2 * n : 0;
+}
+template <typename T, int n> cudaError_t p3_table_fill_n(void *tw2n, cudaStream_t s) {
+    if constexpr (p3_table_len_n<T, n>() == 0) {
+        return cudaSuccess;
+    } else {
+        using K = ColCfg<T, n, COL_FMI>;
+        static_assert(n % (K::R1 * K::R2) == 0, "stage tables cover the two-stage schedule");
+        k_p3_table<T, n, K::R1, K::R2><<<(2 * n + 255) / 256, 256, 0, s>>>(reinterpret_cast<cx_t<T> *>(tw2n));
+        return cudaGetLastError();
+    }
+}
+
 template <typename T, int n, int MODE> cudaError_t launch_col_n(const ColArgs &a, int nbatch, cudaStream_t s) {
     using K = ColCfg<T, n, MODE>;
     if constexpr (!K::Ok) {
@@ -1085,6 +1160,10 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
     }                                                                                                          \
     template <> cudaError_t p3<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
         return launch_col<T, COL_FMI>(2 * N, a, nb, s);                                                        \
+    }                                                                                                          \
+    template <> int p3_table_len<T>(int N) { return N == 256 ? p3_table_len_n<T, 512>() : 0; }                 \
+    template <> cudaError_t p3_table_fill<T>(int N, void *tw2n, cudaStream_t s) {                               \
+        return N == 256 ? p3_table_fill_n<T, 512>(tw2n, s) : cudaSuccess;                                      \
     }                                                                                                          \
     template <> cudaError_t p4<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
         return launch_col<T, COL_INV>(2 * N, a, nb, s);                                                        \

@@ -45,6 +45,12 @@ template <typename T> bool has(int N);
 template <typename T> cudaError_t p1(int N, const RowArgs &a, cudaStream_t s);
 template <typename T> cudaError_t p2(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 template <typename T> cudaError_t p3(int N, const ColArgs &a, int nbatch, cudaStream_t s);
+// The cubic P3 of some sizes reads its twiddles from per-stage tables stored
+// right after the 2N roots in the same buffer (ColArgs::tw): p3_table_len
+// complex entries (0: none), written by p3_table_fill from the roots, which
+// must already be in place.  Every buffer handed to p3 as tw must hold them.
+template <typename T> int p3_table_len(int N);
+template <typename T> cudaError_t p3_table_fill(int N, void *tw2n, cudaStream_t s);
 template <typename T> cudaError_t p4(int N, const ColArgs &a, int nbatch, cudaStream_t s);
 template <typename T> cudaError_t p5(int N, const RowArgs &a, cudaStream_t s);
 // A column pass (mode COL_FWD, COL_INV or COL_FMI) of length n on a non-cubic

@@ -101,7 +101,7 @@ def profile_case(args):
     print(json.dumps({"profile_case": args.profile_case, "N": N, "ok": True, "launches_per_solve": cases}))
 
 
-PASS_KERNELS = ("k_fast_", "k_plane_", "k_p3_tma")  # the solve passes of the profile cases (N = 256)
+PASS_KERNELS = ("k_fast_", "k_lane_", "k_plane_", "k_p3_tma")  # the solve passes of the profile cases (N = 256)
 
 
 def read_ncu_csv(path):

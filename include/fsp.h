@@ -200,10 +200,11 @@ fsp_status fsp_solve_host(fsp_plan *plan, const void *rho_host, void *phi_host, 
 /*
  * fsp_solve_host_many -- `count` solves of HOST arrays, pipelined: the copy of
  * source i+1 to the device and the copy of result i-1 back to the host run on
- * their own streams while solve i runs on `stream`, through two device
- * staging pairs.  rho_host[i], phi_host[i]: host pointers (pinned for
+ * their own streams while solve i runs on `stream`, through three device
+ * staging slots (each copy may take as long as two solves before it holds up
+ * the next solve).  rho_host[i], phi_host[i]: host pointers (pinned for
  * asynchronous, full-bandwidth copies), N^3 reals of the plan's dtype.  The
- * first call allocates four N^3 staging buffers, two streams and six events,
+ * first call allocates six N^3 staging buffers, two streams and nine events,
  * kept by the plan.  Returns after every result is on the host.
  */
 fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void *const *phi_host, int count,

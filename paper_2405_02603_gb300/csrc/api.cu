@@ -38,6 +38,9 @@ namespace {
 
 constexpr uint64_t kMagic = 0x46535050'4c414e31ULL;  // "FSPPLAN1"
 constexpr int kMaxN = 1024;
+// device staging slots of the host-buffer pipeline (fsp_solve_host_many):
+// with three, a step's copies have the time of two solves to finish
+constexpr int kPipeSlots = 3;
 constexpr double kAlpha = 1.1;  // Vico-Greengard window factor (Sec. 2.3)
 
 std::mutex g_mu;
@@ -489,10 +492,10 @@ struct fsp_plan {
     size_t rsize = 8;  // bytes per real
     void *S = nullptr, *W1 = nullptr, *W2 = nullptr, *tw_n = nullptr, *tw_2n = nullptr;
     void *stage_rho = nullptr, *stage_phi = nullptr;
-    // pipelined host solves: two staging pairs, copy streams, events
-    void *pipe_rho[2] = {}, *pipe_phi[2] = {};
+    // pipelined host solves: kPipeSlots staging slots, copy streams, events
+    void *pipe_rho[kPipeSlots] = {}, *pipe_phi[kPipeSlots] = {};
     cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
-    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
+    cudaEvent_t ev_in[kPipeSlots] = {}, ev_comp[kPipeSlots] = {}, ev_out[kPipeSlots] = {};
     TileCfg row, col;
     bool fast = false;  // specialised power-of-two kernels (fast.cuh) serve this N
     bool p3_tma = false;  // P3 by the TMA-staged persistent kernel (p3_tma.cuh)
@@ -531,13 +534,15 @@ size_t plan_points(const fsp_plan *p) {
 }
 
 void plan_free(fsp_plan *p) {
-    for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi, p->pipe_rho[0], p->pipe_rho[1],
-                    p->pipe_phi[0], p->pipe_phi[1], p->SF[0], p->SF[1], p->SF[2], p->W3, p->tw_y, p->tw_z,
-                    (void *)p->err})
+    for (void *q : {p->S, p->W1, p->W2, p->tw_n, p->tw_2n, p->stage_rho, p->stage_phi, p->SF[0], p->SF[1], p->SF[2],
+                    p->W3, p->tw_y, p->tw_z, (void *)p->err})
         if (q) dev_free(q);
+    for (int i = 0; i < kPipeSlots; ++i)
+        for (void *q : {p->pipe_rho[i], p->pipe_phi[i]})
+            if (q) dev_free(q);
     for (cudaStream_t q : {p->pipe_h2d, p->pipe_d2h})
         if (q) cudaStreamDestroy(q);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < kPipeSlots; ++i)
         for (cudaEvent_t q : {p->ev_in[i], p->ev_comp[i], p->ev_out[i]})
             if (q) cudaEventDestroy(q);
     p->magic = 0;
@@ -1351,18 +1356,19 @@ fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void
     if (dev != plan->device) return FSP_EINVAL;
     if (count == 0) return FSP_OK;
     const size_t bytes = plan_points(plan) * plan->rsize;
-    if (!plan->pipe_h2d) {  // first use: staging pairs, copy streams, events
+    if (!plan->pipe_h2d) {  // first use: staging slots, copy streams, events
         GuardScope guard_scope(plan->guarded);
-        DevBuf a0, a1, b0, b1;
+        DevBuf a[kPipeSlots], b[kPipeSlots];
         fsp_status st;
-        if ((st = alloc_or_nomem(a0, bytes)) != FSP_OK || (st = alloc_or_nomem(a1, bytes)) != FSP_OK ||
-            (st = alloc_or_nomem(b0, bytes)) != FSP_OK || (st = alloc_or_nomem(b1, bytes)) != FSP_OK)
-            return st;
+        for (int i = 0; i < kPipeSlots; ++i)
+            if ((st = alloc_or_nomem(a[i], bytes)) != FSP_OK || (st = alloc_or_nomem(b[i], bytes)) != FSP_OK)
+                return st;
         cudaStream_t h2d = nullptr, d2h = nullptr;
-        cudaEvent_t ev[6] = {};
+        cudaEvent_t ev[3 * kPipeSlots] = {};
         bool ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess;
-        for (int i = 0; i < 6 && ok; ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 3 * kPipeSlots && ok; ++i)
+            ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
             for (cudaStream_t q : {h2d, d2h})
                 if (q) cudaStreamDestroy(q);
@@ -1370,28 +1376,30 @@ fsp_status fsp_solve_host_many(fsp_plan *plan, const void *const *rho_host, void
                 if (q) cudaEventDestroy(q);
             return FSP_ECUDA;
         }
-        plan->pipe_rho[0] = a0.release(), plan->pipe_rho[1] = a1.release();
-        plan->pipe_phi[0] = b0.release(), plan->pipe_phi[1] = b1.release();
+        for (int i = 0; i < kPipeSlots; ++i) {
+            plan->pipe_rho[i] = a[i].release(), plan->pipe_phi[i] = b[i].release();
+            plan->ev_in[i] = ev[i], plan->ev_comp[i] = ev[kPipeSlots + i], plan->ev_out[i] = ev[2 * kPipeSlots + i];
+        }
         plan->pipe_h2d = h2d, plan->pipe_d2h = d2h;
-        for (int i = 0; i < 2; ++i) plan->ev_in[i] = ev[i], plan->ev_comp[i] = ev[2 + i], plan->ev_out[i] = ev[4 + i];
-        plan->bytes += 4 * bytes;
+        plan->bytes += 2 * kPipeSlots * bytes;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // all three streams start after prior work on `stream`
     cudaError_t e = cudaEventRecord(plan->ev_out[0], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->pipe_h2d, plan->ev_out[0], 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->pipe_d2h, plan->ev_out[0], 0);
-    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_comp[0], s);
-    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_comp[1], s);
-    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[1], s);
+    for (int k = 0; k < kPipeSlots && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(plan->ev_comp[k], s);
+        if (e == cudaSuccess && k > 0) e = cudaEventRecord(plan->ev_out[k], s);
+    }
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
-        const int k = i & 1;
-        // copy in: slot k's source buffer is free once the solve of i-2 ran
+        const int k = i % kPipeSlots;
+        // copy in: slot k's source buffer is free once the solve of i-3 ran
         e = cudaStreamWaitEvent(plan->pipe_h2d, plan->ev_comp[k], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(plan->pipe_rho[k], rho_host[i], bytes, cudaMemcpyHostToDevice, plan->pipe_h2d);
         if (e == cudaSuccess) e = cudaEventRecord(plan->ev_in[k], plan->pipe_h2d);
-        // solve: after its copy-in and after the copy-out of i-2 freed slot k
+        // solve: after its copy-in and after the copy-out of i-3 freed slot k
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->ev_in[k], 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->ev_out[k], 0);
         if (e == cudaSuccess) e = enqueue_solve_ws(plan, plan->pipe_rho[k], plan->pipe_phi[k], plan->W1, plan->W2, s);
@@ -1469,10 +1477,11 @@ fsp_status fsp_plan_check_bounds(const fsp_plan *plan, unsigned long long *bad_b
     if (!plan->guarded) return FSP_EUNSUPPORTED;
     if (cudaDeviceSynchronize() != cudaSuccess) return FSP_ECUDA;
     const fsp_plan *p = plan;
-    const void *bufs[] = {p->S,          p->W1,          p->W2,          p->tw_n,  p->tw_2n, p->stage_rho,
-                          p->stage_phi,  p->pipe_rho[0], p->pipe_rho[1], p->pipe_phi[0], p->pipe_phi[1],
-                          p->SF[0],      p->SF[1],       p->SF[2],       p->W3,    p->tw_y,  p->tw_z,
-                          (const void *)p->err};
+    const void *bufs[] = {p->S,          p->W1,          p->W2,          p->tw_n,        p->tw_2n,
+                          p->stage_rho,  p->stage_phi,   p->pipe_rho[0], p->pipe_rho[1], p->pipe_rho[2],
+                          p->pipe_phi[0], p->pipe_phi[1], p->pipe_phi[2], p->SF[0],      p->SF[1],
+                          p->SF[2],      p->W3,          p->tw_y,        p->tw_z,        (const void *)p->err};
+    static_assert(kPipeSlots == 3, "the list above names every staging slot");
     for (const void *q : bufs) {
         if (!q) continue;
         Guarded g{nullptr, 0};

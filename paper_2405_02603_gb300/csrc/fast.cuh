@@ -417,6 +417,7 @@ template <typename T, int MODE, int n> struct ColOpt {
     // TT: the twiddled stages of the cubic P3 read per-stage tables [j][r]
     // (after the n roots; see p3_table_fill): a pair of twiddles per 16-byte
     // load at an immediate offset, no index arithmetic per twiddle
+    // (measured: N = 256 P3 0.191 -> 0.183 ms; N = 128 2 % slower, so off there)
     static constexpr bool TT = MODE == COL_FMI && F32 && n == 512;
     static constexpr bool TWS = (DF && MODE != COL_INV) || (MODE == COL_FMO && !std::is_same<T, double>::value) ||
                                 (MODE == COL_FMI && F32 && n == 1024);
@@ -1161,9 +1162,23 @@ template <typename T, bool R2C> cudaError_t launch_row(int N, const RowArgs &a, 
     template <> cudaError_t p3<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
         return launch_col<T, COL_FMI>(2 * N, a, nb, s);                                                        \
     }                                                                                                          \
-    template <> int p3_table_len<T>(int N) { return N == 256 ? p3_table_len_n<T, 512>() : 0; }                 \
+    template <> int p3_table_len<T>(int N) {                                                                   \
+        switch (N) {                                                                                           \
+        case 32: return p3_table_len_n<T, 64>();                                                               \
+        case 64: return p3_table_len_n<T, 128>();                                                              \
+        case 128: return p3_table_len_n<T, 256>();                                                             \
+        case 256: return p3_table_len_n<T, 512>();                                                             \
+        }                                                                                                      \
+        return 0;                                                                                              \
+    }                                                                                                          \
     template <> cudaError_t p3_table_fill<T>(int N, void *tw2n, cudaStream_t s) {                               \
-        return N == 256 ? p3_table_fill_n<T, 512>(tw2n, s) : cudaSuccess;                                      \
+        switch (N) {                                                                                           \
+        case 32: return p3_table_fill_n<T, 64>(tw2n, s);                                                       \
+        case 64: return p3_table_fill_n<T, 128>(tw2n, s);                                                      \
+        case 128: return p3_table_fill_n<T, 256>(tw2n, s);                                                     \
+        case 256: return p3_table_fill_n<T, 512>(tw2n, s);                                                     \
+        }                                                                                                      \
+        return cudaSuccess;                                                                                    \
     }                                                                                                          \
     template <> cudaError_t p4<T>(int N, const ColArgs &a, int nb, cudaStream_t s) {                            \
         return launch_col<T, COL_INV>(2 * N, a, nb, s);                                                        \

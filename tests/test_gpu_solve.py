@@ -151,13 +151,18 @@ def test_solve_host_many_matches_device(fsp, dtype):
     import torch
     N = 64
     p = fsp.Plan(N, 1.0, "vg_dct", dtype)
-    srcs = [I.gaussian_mixture(N, seed=s) for s in range(5)]
+    srcs = [I.gaussian_mixture(N, seed=s) for s in range(7)]  # every staging slot used twice or more
     tdt = fsp.torch_dtype(dtype)
     hin = [torch.from_numpy(x).to(tdt).pin_memory() for x in srcs]
     hout = [torch.empty_like(h).pin_memory() for h in hin]
     p.solve_host_many(hin, hout)
     for h, o in zip(hin, hout):
         assert torch.equal(o, p.solve(h.cuda()).cpu())
+    # a second call starts on the slots and events the first one left
+    back = [torch.empty_like(h).pin_memory() for h in hin]
+    p.solve_host_many(hin[::-1], back)
+    for o, b in zip(hout[::-1], back):
+        assert torch.equal(o, b)
     p.solve_host_many([], [])  # nothing to do
 
 

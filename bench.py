@@ -226,7 +226,7 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ["fast.cuh", "fast.h", "fast_f32.cu", "fast_f64.cu", "fast_df.cu", "df.cuh", "fft_engine.cuh",
+KERNEL_SOURCES = ["fast.cuh", "fast_col_body.inc", "fast.h", "fast_f32.cu", "fast_f64.cu", "fast_df.cu", "df.cuh", "fft_engine.cuh",
                   "kernels.cuh"]
 
 

@@ -104,10 +104,27 @@ template <int I, int E> struct StaticFor {
 
 // ------------------------------------------------------- register DFTs --
 // v'[q] = sum_r v[r] exp(D 2 pi i r q / R).  HZ: inputs r >= R/2 are zero
-// (not read).  HO: only outputs q < R/2 are produced.
-template <typename T, int D> struct RD {
+// (not read).  HO: only outputs q < R/2 are produced.  PK (FP32 only): the
+// complex sums as packed two-float instructions (cadd_pk, csub_pk) and the
+// +-i rotations of the radix-4 butterflies per component, so that no pair
+// has to be rebuilt for the packed form; kernels choose it where it
+// measured faster.
+template <typename T, int D, bool PK = false> struct RD {
     using C = cx_t<T>;
+    static_assert(!PK || std::is_same<T, float>::value, "packed sums are FP32");
     static __device__ __forceinline__ C rot(C a) { return D < 0 ? cmulmi(a) : cmuli(a); }  // exp(D i pi/2)
+    static __device__ __forceinline__ C add(C a, C b) {
+        if constexpr (PK)
+            return cadd_pk(a, b);
+        else
+            return cadd(a, b);
+    }
+    static __device__ __forceinline__ C sub(C a, C b) {
+        if constexpr (PK)
+            return csub_pk(a, b);
+        else
+            return csub(a, b);
+    }
 
     // multiply by exp(D 2 pi i M / 32)
     template <int M> static __device__ __forceinline__ C w32(C a) {
@@ -126,20 +143,12 @@ template <typename T, int D> struct RD {
         }
     }
 
-    // t + rot(d) and t - rot(d).  FP32 writes them per component (the sign
-    // folds into the scalar adds), so only the plain complex sums take the
-    // packed two-float form; the other types use the complex helpers.
+    // t + rot(d) and t - rot(d) per component (PK; the sign folds into the adds)
     static __device__ __forceinline__ C addrot(C t, C d) {
-        if constexpr (std::is_same<T, float>::value)
-            return D < 0 ? C{t.x + d.y, t.y - d.x} : C{t.x - d.y, t.y + d.x};
-        else
-            return cadd(t, rot(d));
+        return D < 0 ? C{t.x + d.y, t.y - d.x} : C{t.x - d.y, t.y + d.x};
     }
     static __device__ __forceinline__ C subrot(C t, C d) {
-        if constexpr (std::is_same<T, float>::value)
-            return D < 0 ? C{t.x - d.y, t.y + d.x} : C{t.x + d.y, t.y - d.x};
-        else
-            return csub(t, rot(d));
+        return D < 0 ? C{t.x - d.y, t.y + d.x} : C{t.x + d.y, t.y - d.x};
     }
 
     template <bool HZ, bool HO> static __device__ __forceinline__ void d2(C *v) {
@@ -147,23 +156,39 @@ template <typename T, int D> struct RD {
             v[1] = v[0];
         } else {
             const C a = v[0], b = v[1];
-            v[0] = cadd(a, b);
-            if constexpr (!HO) v[1] = csub(a, b);
+            v[0] = add(a, b);
+            if constexpr (!HO) v[1] = sub(a, b);
         }
     }
     template <bool HZ, bool HO> static __device__ __forceinline__ void d4(C *v) {
-        C t0, t1, t2, d;  // outputs 1 and 3 are t1 +- rot(d)
-        if constexpr (HZ) {
-            t0 = v[0], t1 = v[0], t2 = v[1], d = v[1];
+        if constexpr (PK) {
+            C t0, t1, t2, d;  // outputs 1 and 3 are t1 +- rot(d)
+            if constexpr (HZ) {
+                t0 = v[0], t1 = v[0], t2 = v[1], d = v[1];
+            } else {
+                t0 = add(v[0], v[2]), t1 = sub(v[0], v[2]);
+                t2 = add(v[1], v[3]), d = sub(v[1], v[3]);
+            }
+            v[0] = add(t0, t2);
+            v[1] = addrot(t1, d);
+            if constexpr (!HO) {
+                v[2] = sub(t0, t2);
+                v[3] = subrot(t1, d);
+            }
         } else {
-            t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-            t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
-        }
-        v[0] = cadd(t0, t2);
-        v[1] = addrot(t1, d);
-        if constexpr (!HO) {
-            v[2] = csub(t0, t2);
-            v[3] = subrot(t1, d);
+            C t0, t1, t2, t3;
+            if constexpr (HZ) {
+                t0 = v[0], t1 = v[0], t2 = v[1], t3 = rot(v[1]);
+            } else {
+                t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+                t2 = cadd(v[1], v[3]), t3 = rot(csub(v[1], v[3]));
+            }
+            v[0] = cadd(t0, t2);
+            v[1] = cadd(t1, t3);
+            if constexpr (!HO) {
+                v[2] = csub(t0, t2);
+                v[3] = csub(t1, t3);
+            }
         }
     }
     template <bool HZ, bool HO> static __device__ __forceinline__ void d8(C *v) {
@@ -173,12 +198,22 @@ template <typename T, int D> struct RD {
         d4<HZ, false>(e);
         d4<HZ, false>(o);
         o[1] = w32<4>(o[1]);
-        o[3] = w32<12>(o[3]);  // o[2] takes w32<8> = rot in addrot / subrot
-        v[0] = cadd(e[0], o[0]), v[1] = cadd(e[1], o[1]);
-        v[2] = addrot(e[2], o[2]), v[3] = cadd(e[3], o[3]);
-        if constexpr (!HO) {
-            v[4] = csub(e[0], o[0]), v[5] = csub(e[1], o[1]);
-            v[6] = subrot(e[2], o[2]), v[7] = csub(e[3], o[3]);
+        o[3] = w32<12>(o[3]);
+        if constexpr (PK) {  // o[2] takes w32<8> = rot in addrot / subrot
+            v[0] = add(e[0], o[0]), v[1] = add(e[1], o[1]);
+            v[2] = addrot(e[2], o[2]), v[3] = add(e[3], o[3]);
+            if constexpr (!HO) {
+                v[4] = sub(e[0], o[0]), v[5] = sub(e[1], o[1]);
+                v[6] = subrot(e[2], o[2]), v[7] = sub(e[3], o[3]);
+            }
+        } else {
+            o[2] = w32<8>(o[2]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = cadd(e[q], o[q]);
+            if constexpr (!HO) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q + 4] = csub(e[q], o[q]);
+            }
         }
     }
     // R = 4 B (B = 4 or 8): x[B n1 + n2] -> DFT_4 over n1 per n2, twiddle
@@ -215,12 +250,12 @@ template <typename T, int D> struct RD {
     template <bool HZ, bool HO> static __device__ __forceinline__ void d3(C *v) {
         static_assert(!HZ && !HO, "radix 3 runs only as a middle stage");
         constexpr T s3 = T(D * 0.86602540378443864676372317075294);
-        const C a = v[0], t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        const C a = v[0], t = add(v[1], v[2]), d = sub(v[1], v[2]);
         const C u = C{a.x - T(0.5) * t.x, a.y - T(0.5) * t.y};
         const C w = C{-s3 * d.y, s3 * d.x};
-        v[0] = cadd(a, t);
-        v[1] = cadd(u, w);
-        v[2] = csub(u, w);
+        v[0] = add(a, t);
+        v[1] = add(u, w);
+        v[2] = sub(u, w);
     }
     // Radix 5: with t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4, t4 = v2 - v3,
     // X1,4 = v0 + c1 t1 + c2 t2 +- i D (s1 t3 + s2 t4), X2,3 = v0 + c2 t1 +
@@ -229,8 +264,8 @@ template <typename T, int D> struct RD {
         static_assert(!HZ && !HO, "radix 5 runs only as a middle stage");
         constexpr T c1 = T(0.30901699437494742410229341718282), c2 = T(-0.80901699437494742410229341718282);
         constexpr T s1 = T(D * 0.95105651629515357211643933337938), s2 = T(D * 0.58778525229247312916870595463907);
-        const C v0 = v[0], t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]),
-                t4 = csub(v[2], v[3]);
+        const C v0 = v[0], t1 = add(v[1], v[4]), t2 = add(v[2], v[3]), t3 = sub(v[1], v[4]),
+                t4 = sub(v[2], v[3]);
         const C m1 = C{v0.x + c1 * t1.x + c2 * t2.x, v0.y + c1 * t1.y + c2 * t2.y};
         const C m2 = C{v0.x + c2 * t1.x + c1 * t2.x, v0.y + c2 * t1.y + c1 * t2.y};
         const C n1 = C{s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y};
@@ -251,9 +286,9 @@ template <typename T, int D> struct RD {
         d3<false, false>(o);
         const C o1 = C{T(0.5) * o[1].x - s3 * o[1].y, s3 * o[1].x + T(0.5) * o[1].y};    // w6 o1
         const C o2 = C{-T(0.5) * o[2].x - s3 * o[2].y, s3 * o[2].x - T(0.5) * o[2].y};   // w6^2 o2
-        v[0] = cadd(e[0], o[0]), v[3] = csub(e[0], o[0]);
-        v[1] = cadd(e[1], o1), v[4] = csub(e[1], o1);
-        v[2] = cadd(e[2], o2), v[5] = csub(e[2], o2);
+        v[0] = add(e[0], o[0]), v[3] = sub(e[0], o[0]);
+        v[1] = add(e[1], o1), v[4] = sub(e[1], o1);
+        v[2] = add(e[2], o2), v[5] = sub(e[2], o2);
     }
     template <int R, bool HZ, bool HO> static __device__ __forceinline__ void dft(C *v) {
         if constexpr (R == 2)
@@ -277,7 +312,7 @@ template <typename T, int D> struct RD {
 // n: transform length; V: values per thread; L: lines per CTA (pitch L+1).
 // TWS: the roots table is in shared memory (generic loads) rather than read
 // through the read-only global path.
-template <typename T, int D, int n, int V, int L, bool TWS = false> struct Stg {
+template <typename T, int D, int n, int V, int L, bool TWS = false, bool PK = false> struct Stg {
     using C = cx_t<T>;
     static constexpr int TPL = n / V;
     static constexpr int LD = L + 1;
@@ -305,7 +340,7 @@ template <typename T, int D, int n, int V, int L, bool TWS = false> struct Stg {
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], twid(tw, (int)(r * j) * tws));
             }
-            RD<T, D>::template dft<R, HZ, HO>(v + k * R);
+            RD<T, D, PK>::template dft<R, HZ, HO>(v + k * R);
         });
     }
 
@@ -326,7 +361,7 @@ template <typename T, int D, int n, int V, int L, bool TWS = false> struct Stg {
                 if (q > 0) v[k * R + 2 * q] = cmul(v[k * R + 2 * q], w0);
                 v[k * R + 2 * q + 1] = cmul(v[k * R + 2 * q + 1], w1);
             }
-            RD<T, D>::template dft<R, HZ, HO>(v + k * R);
+            RD<T, D, PK>::template dft<R, HZ, HO>(v + k * R);
         });
     }
 
@@ -353,9 +388,10 @@ template <typename T, int D, int n, int V, int L, bool TWS = false> struct Stg {
 // registers: exchange through shared memory, compute; leaves the last
 // stage's outputs in registers.  `first_sync` is needed when shared memory
 // was read just before (the caller's previous stage loaded from it).
-template <typename T, int D, int n, int V, int L, int R1, int R2, int R3, bool HO_LAST, bool TWS = false>
+template <typename T, int D, int n, int V, int L, int R1, int R2, int R3, bool HO_LAST, bool TWS = false,
+          bool PK = false>
 __device__ __forceinline__ void run_rest(cx_t<T> *v, cx_t<T> *buf, int t, int l, const cx_t<T> *tw, bool first_sync) {
-    using S = Stg<T, D, n, V, L, TWS>;
+    using S = Stg<T, D, n, V, L, TWS, PK>;
     if (first_sync) __syncthreads();
     S::template store_out<R1, 1>(buf, v, t, l);
     __syncthreads();
@@ -414,6 +450,13 @@ template <typename T, int MODE, int n> struct ColOpt {
     // CTAs per SM the register allocation must allow (2: k_fast_col_occ2):
     // two 256-thread tiles of the FP32 P3 on lines of 512 (N = 256)
     static constexpr int MINB = ZL && F32 && n == 512 ? 2 : 1;
+    // PK: packed two-float complex sums in the register DFTs, on the FP32
+    // lines of 512 of P3 (0.206 -> 0.191 ms) and P2 (0.090 -> 0.084 ms);
+    // P4 unchanged by them, the lines of 1024 6-8 % slower, so off there
+    static constexpr bool PK = F32 && n == 512 && (ZL || MODE == COL_FWD);
+    // INL: k_fast_col_inl for the FP32 P2 on lines of 512 (0.084 ms against
+    // 0.088 with the body in the kernel)
+    static constexpr bool INL = F32 && n == 512 && MODE == COL_FWD;
     // TT: the twiddled stages of the cubic P3 read per-stage tables [j][r]
     // (after the n roots; see p3_table_fill): a pair of twiddles per 16-byte
     // load at an immediate offset, no index arithmetic per twiddle
@@ -426,202 +469,38 @@ template <typename T, int MODE, int n> struct ColOpt {
 // RG (a non-cubic box): the strides, the number of lines (k_x <= n_x) and the
 // fold of the batch index (k_y <= n_y) come from the arguments instead of
 // ColGeo; the cube keeps its compile-time geometry.
+// The column pass kernels, one body source (fast_col_body.inc).  k_fast_col:
+// the body in the kernel, the plain launch bound.  k_fast_col_occ2: a bound
+// of two CTAs per SM (ColOpt::MINB), the body inlined from fast_col_body.
+// k_fast_col_inl: the plain bound, the body inlined (ColOpt::INL).  The
+// compiler's code differs between the forms; each pass takes the one it
+// measured fastest with.
 template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG>
 __device__ __forceinline__ void fast_col_body(const ColArgs &a) {
-    using C = cx_t<T>;
-    using G = ColGeo<n, MODE>;
-    constexpr int TPL = n / V, N = G::N;
-    constexpr int RL = LastR<R1, R2, R3>::value;
-    const long long IN_POS = RG ? a.in_pos : G::IN_POS, IN_BATCH = RG ? a.in_batch : G::IN_BATCH;
-    const long long OUT_POS = RG ? a.out_pos : G::OUT_POS, OUT_BATCH = RG ? a.out_batch : G::OUT_BATCH;
-    const long long S_POS = RG ? a.s_pos : G::S_POS, S_BATCH = RG ? a.s_batch : G::S_BATCH;
-    const int HB = RG ? a.half_b : N;  // fold of the batch index in P3
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
-    const int l = threadIdx.x % L, t = threadIdx.x / L;
-    // Main tiles: lines (k_x) [bx*L, bx*L + L) of batch row by - X, all < N.
-    // The Nyquist column k_x = N runs in the first X = NB/N block rows, whose
-    // tile's L lines are L consecutive batch indices of that one column (their
-    // loads are strided, so they go first rather than form the last wave).
-    // RG: N -> n_x = nlines - 1 and X = a.xrows rows of gridDim.x tiles.
-    int line;
-    long long bt;
-    if constexpr (!RG) {
-        constexpr int NB = G::ZL ? 2 * N : N;  // batch rows (k_y or z)
-        constexpr int X = NB / N;
-        if ((int)blockIdx.y >= X) {
-            line = blockIdx.x * L + l;
-            bt = blockIdx.y - X;
-        } else {
-            line = N;
-            bt = ((long long)blockIdx.y * (N / L) + blockIdx.x) * L + l;
-        }
-    } else {
-        if ((int)blockIdx.y >= a.xrows) {
-            line = blockIdx.x * L + l;
-            bt = blockIdx.y - a.xrows;
-        } else {
-            const long long q = (long long)blockIdx.y * gridDim.x + blockIdx.x;  // Nyquist tile
-            if (q * L >= a.nbatch) return;  // the whole block: before any barrier
-            line = a.nlines - 1;
-            bt = q * L + l;
-        }
-    }
-    constexpr bool ok = true;
-    using O = ColOpt<T, MODE, n>;
-    const C *tw = reinterpret_cast<const C *>(a.tw);
-    if constexpr (O::TWS) {
-        // the roots table in shared memory after the exchange buffer (first
-        // read after the barrier that opens the second stage)
-        C *tws = buf + (size_t)n * (L + 1);
-        for (int e = threadIdx.x; e < n; e += L * TPL) tws[e] = ldg_c(tw + e);
-        tw = tws;
-    }
-    // thread-relative bases: position p = t + c lives at base_t + c*POS
-    const C *in_t = reinterpret_cast<const C *>(a.in) + bt * IN_BATCH + line + (long long)t * IN_POS;
-    C *out_t = reinterpret_cast<C *>(a.out) + bt * OUT_BATCH + line + (long long)t * OUT_POS;
-    C v[V];
-
-    // stage 0 inputs straight from global memory
-    constexpr bool HZ0 = MODE != COL_INV;
-    constexpr int D0 = MODE == COL_INV ? +1 : -1;
-    StaticFor<0, V / R1>::run([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        StaticFor<0, HZ0 ? R1 / 2 : R1>::run([&](auto rc) {
-            constexpr int r = decltype(rc)::value;
-            constexpr long long c = k * TPL + r * (n / R1);
-            v[k * R1 + r] = ok ? ldcg_c(in_t + c * IN_POS) : C{T(0), T(0)};
-        });
-    });
-    if constexpr (O::PF) {
-        // prefetch this thread's spectrum values into L1: their latency then
-        // overlaps the forward transform instead of stalling the multiply
-        const int fy0 = (int)bt <= HB ? (int)bt : 2 * HB - (int)bt;
-        const T *Sy0 = reinterpret_cast<const T *>(a.S) + (long long)fy0 * S_BATCH + line;
-        StaticFor<0, V / RL>::run([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            StaticFor<0, RL>::run([&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                constexpr int c = k * TPL + r * (n / RL);
-                const int p = t + c;
-                const int fz = p <= N ? p : n - p;
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(Sy0 + (long long)fz * S_POS));
-            });
-        });
-    }
-    // per-stage twiddle tables after the n roots: the forward's second stage
-    // (radix R2 over Ns = R1) at tw + n, the inverse's (R1 over R2) at tw + 2n
-    constexpr bool TT = O::TT && !RG && R3 == 1;
-    Stg<T, D0, n, V, L, O::TWS>::template compute<R1, 1, HZ0, false>(v, t, tw);
-    if constexpr (TT) {
-        using SF = Stg<T, D0, n, V, L>;
-        SF::template store_out<R1, 1>(buf, v, t, l);
-        __syncthreads();
-        SF::template load_in<R2>(v, buf, t, l);
-        SF::template compute_tt<R2, R1, false, false>(v, t, tw + n);
-    } else {
-        run_rest<T, D0, n, V, L, R1, R2, R3, MODE == COL_INV, O::TWS>(v, buf, t, l, tw, false);
-    }
-
-    if constexpr (G::ZL) {
-        // multiply by the real, even spectrum at the folded frequency
-        // min(p, n - p); for most registers the branch is known at compile time
-        const int fy = (int)bt <= HB ? (int)bt : 2 * HB - (int)bt;
-        const T *Sy = reinterpret_cast<const T *>(a.S) + (long long)fy * S_BATCH + line;
-        const T *S_up = Sy + (long long)t * S_POS, *S_dn = Sy - (long long)t * S_POS;
-        // COL_FMO (a field component): the spectrum is odd in z (a.odd = 1),
-        // k_y (2) or k_x (3); the multiplier is -i S[fold], negated past the
-        // fold in z (per register) or k_y (per thread); k_x <= N never flips
-        const T sy = MODE == COL_FMO && a.odd == 2 && (int)bt > HB ? T(-1) : T(1);
-        const bool oz = MODE == COL_FMO && a.odd == 1;
-        StaticFor<0, V / RL>::run([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            StaticFor<0, RL>::run([&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                constexpr int c = k * TPL + r * (n / RL);
-                T s;
-                bool upper;  // z = t + c > N
-                if constexpr (c + TPL - 1 <= N) {
-                    s = ok ? S_up[(long long)c * S_POS] : T(0);
-                    upper = false;
-                } else if constexpr (c > N) {
-                    s = ok ? S_dn[(long long)(n - c) * S_POS] : T(0);
-                    upper = true;
-                } else {
-                    const int p = t + c;
-                    const int fz = p <= N ? p : n - p;
-                    s = ok ? Sy[(long long)fz * S_POS] : T(0);
-                    upper = p > N;
-                }
-                if constexpr (MODE == COL_FMI) {
-                    v[k * RL + r].x *= s;
-                    v[k * RL + r].y *= s;
-                } else {
-                    if (oz && upper) s = -s;
-                    s *= sy;
-                    const C w = v[k * RL + r];
-                    v[k * RL + r] = C{s * w.y, -(s * w.x)};
-                }
-            });
-        });
-        // inverse, radix schedule reversed: its stage 0 is the forward's last
-        // radix on the same butterflies, already in registers
-        using SI = Stg<T, +1, n, V, L, O::TWS>;
-        if constexpr (R3 > 1) {
-            SI::template compute<R3, 1, false, false>(v, t, tw);
-            run_rest<T, +1, n, V, L, R3, R2, R1, true, O::TWS>(v, buf, t, l, tw, true);
-        } else {
-            SI::template compute<R2, 1, false, false>(v, t, tw);
-            if constexpr (TT) {
-                __syncthreads();
-                SI::template store_out<R2, 1>(buf, v, t, l);
-                __syncthreads();
-                SI::template load_in<R1>(v, buf, t, l);
-                SI::template compute_tt<R1, R2, false, true>(v, t, tw + 2 * n);
-            } else {
-                run_rest<T, +1, n, V, L, R2, R1, 1, true, O::TWS>(v, buf, t, l, tw, true);
-            }
-        }
-        constexpr int RF = R1;  // last radix of the reversed schedule
-        StaticFor<0, V / RF>::run([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            StaticFor<0, RF / 2>::run([&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                constexpr long long c = k * TPL + r * (n / RF);
-                if (ok) out_t[c * OUT_POS] = v[k * RF + r];
-            });
-        });
-    } else {
-        constexpr bool HO = MODE == COL_INV;
-        StaticFor<0, V / RL>::run([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            StaticFor<0, HO ? RL / 2 : RL>::run([&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                constexpr long long c = k * TPL + r * (n / RL);
-                if (ok) out_t[c * OUT_POS] = v[k * RL + r];
-            });
-        });
-    }
+#include "fast_col_body.inc"
 }
-
-// The column kernels: the plain launch bound leaves the register count to
-// the compiler; k_fast_col_occ2 caps it so that two CTAs fit on an SM
-// (ColOpt::MINB), where the compiler would otherwise take a few more.
 template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG = false>
 __global__ void __launch_bounds__(L *(n / V)) k_fast_col(const ColArgs a) {
-    fast_col_body<T, n, V, L, R1, R2, R3, MODE, RG>(a);
+#include "fast_col_body.inc"
 }
 template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG = false>
 __global__ void __launch_bounds__(L *(n / V), 2) k_fast_col_occ2(const ColArgs a) {
+    fast_col_body<T, n, V, L, R1, R2, R3, MODE, RG>(a);
+}
+template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG = false>
+__global__ void __launch_bounds__(L *(n / V)) k_fast_col_inl(const ColArgs a) {
     fast_col_body<T, n, V, L, R1, R2, R3, MODE, RG>(a);
 }
 template <typename T, int n, int V, int L, int R1, int R2, int R3, int MODE, bool RG>
 constexpr auto col_kernel() {
     if constexpr (ColOpt<T, MODE, n>::MINB == 2)
         return k_fast_col_occ2<T, n, V, L, R1, R2, R3, MODE, RG>;
+    else if constexpr (ColOpt<T, MODE, n>::INL)
+        return k_fast_col_inl<T, n, V, L, R1, R2, R3, MODE, RG>;
     else
         return k_fast_col<T, n, V, L, R1, R2, R3, MODE, RG>;
 }
+
 
 // ------------------------------------------------------- row kernels --
 // P1: rows of N reals -> N+1 coefficients of the zero-padded length-2N row,
@@ -808,7 +687,7 @@ template <typename T, int D, int N, int V, int L, int R1>
 __device__ __forceinline__ void lane_row_stages(cx_t<T> *v, cx_t<T> *buf, int t, int l, const cx_t<T> *tw,
                                                 bool hz, bool ho) {
     using X = LaneRow<T, N, V, R1, V, 1>;
-    using S = Stg<T, D, N, V, L>;
+    using S = Stg<T, D, N, V, L, false, true>;  // packed sums (FP32 only, as LaneRow::ok)
     constexpr int TPL = N / V;
     if (hz)
         S::template compute<R1, 1, true, false>(v, t, tw);

@@ -30,12 +30,19 @@ template <typename T> using cx_t = typename cx<T>::t;
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
-#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
 // FP32 complex sums as one packed two-float instruction (add/sub .f32x2,
 // sm_100 and later): each component is rounded exactly as by the scalar add,
-// in half the issue slots -- the butterflies are mostly such sums.
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+// in half the issue slots.  Used where a kernel measured faster with them
+// (the register DFTs' PK option).
+__device__ __forceinline__ float2 cadd_pk(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __fadd2_rn(a, b);
+#else
+    return cadd(a, b);
+#endif
+}
+__device__ __forceinline__ float2 csub_pk(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
     float2 r;
     asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
         "mov.b64 pa, {%2, %3};\n\t"
@@ -45,8 +52,10 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
         : "=f"(r.x), "=f"(r.y)
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return r;
-}
+#else
+    return csub(a, b);
 #endif
+}
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {

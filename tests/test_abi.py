@@ -109,11 +109,38 @@ def test_fft_and_kernel_validation(L):
     assert L.fsp_kernel_T(11, 1.0, 0, None, None) == 2
 
 
+def test_spectrum_restore_validation_needs_no_device(L, tmp_path):
+    """fsp_plan_create_from_spectrum refuses bad arguments before any CUDA
+    call; the binding checks the array shape and the file format first."""
+    import numpy as np
+    import paper_2405_02603_gb300 as fsp
+    out = ctypes.c_void_p()
+    S = np.ones((9, 9, 9))
+    ptr = ctypes.c_void_p(S.ctypes.data)
+    assert L.fsp_plan_create_from_spectrum(None, 8, 1.0, 0, 0, ptr, None) == 1
+    assert L.fsp_plan_create_from_spectrum(ctypes.byref(out), 8, 1.0, 0, 0, None, None) == 1
+    bad = S.copy()
+    bad[4, 4, 4] = np.inf
+    assert L.fsp_plan_create_from_spectrum(ctypes.byref(out), 8, 1.0, 0, 0,
+                                           ctypes.c_void_p(bad.ctypes.data), None) == 1
+    assert out.value is None
+    S7 = np.ones((8, 8, 8))  # 2N = 14 is not 2/3/5-smooth
+    assert L.fsp_plan_create_from_spectrum(ctypes.byref(out), 7, 1.0, 0, 0,
+                                           ctypes.c_void_p(S7.ctypes.data), None) == 2
+    with pytest.raises(fsp.FspError) as ei:
+        fsp.Plan.from_spectrum(8, 1.0, "he", "f64", np.ones((8, 8, 8)))
+    assert ei.value.status == fsp.FSP_EINVAL
+    np.savez(tmp_path / "other.npz", format=np.array("not-a-spectrum"), S=S)
+    with pytest.raises(fsp.FspError) as ei:
+        fsp.Plan.load(tmp_path / "other.npz")
+    assert ei.value.status == fsp.FSP_EINVAL
+
+
 def test_product_does_not_reference_the_oracle():
     pkg = os.path.join(ROOT, "paper_2405_02603_gb300")
     for dirpath, _, files in os.walk(pkg):
         for f in files:
-            if f.endswith((".py", ".cu", ".cuh", ".h")):
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".inc")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "fsp_oracle" not in text, f

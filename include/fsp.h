@@ -500,12 +500,10 @@ fsp_status fsp_host_free(void *p, size_t bytes);
 
 /*
  * fsp_solve_noalloc -- an FP64 solve that allocates no device memory.  The
- * paper has no counterpart: it is an interface for callers that cannot call
- * cudaMalloc (code running while a CUDA graph is captured in global mode,
- * where the runtime rejects allocations; real-time loops that forbid allocator
- * calls; applications whose device memory is entirely held by their own
- * allocator).  The caller passes everything that has a size: the spectrum,
- * the source and the result.
+ * paper has no counterpart: it is an interface for callers that do not call
+ * cudaMalloc (real-time loops that forbid allocator calls; applications whose
+ * device memory is entirely held by their own allocator).  The caller passes
+ * everything that has a size: the spectrum, the source and the result.
  *
  * N    2 <= N <= 32 and 2N 2/3/5-smooth; larger or unsupported sizes return
  *      FSP_EUNSUPPORTED (N < 2: FSP_EINVAL) before any device work.
@@ -520,8 +518,7 @@ fsp_status fsp_host_free(void *p, size_t bytes);
  * up that array's device address in the current context
  * (cudaGetSymbolAddress, which allocates nothing), so the address stays right
  * after a device reset or a new primary context.  The first lookup in a
- * context may load the library's device code: make the first call on a device
- * before any stream capture.  All calls on a
+ * context may load the library's device code.  All calls on a
  * device share the one array and leave their intermediate values in it; no
  * part of it needs to start at zero (each call writes every element before
  * reading it).  Calls whose device work overlaps in time (different streams,

@@ -2,12 +2,10 @@
 // workspace in a fixed, statically allocated device array instead of memory
 // obtained from cudaMalloc.
 //
-// Why it exists: some callers cannot call cudaMalloc at all.  Code that runs
-// while another thread of the process captures a CUDA graph in global mode
-// gets allocation calls rejected by the runtime; real-time loops often forbid
-// any allocator call; and some host applications reserve all device memory
-// through their own allocator and hand out only the buffers they own.  Such a
-// caller can still compute a potential here: it passes the spectrum, the
+// Why it exists: some callers do not call cudaMalloc at all.  Real-time
+// loops often forbid any allocator call, and some host applications reserve
+// all device memory through their own allocator and hand out only the
+// buffers they own.  Such a caller can still compute a potential here: it passes the spectrum, the
 // source and the result buffer, and the solve borrows its scratch from the
 // array below.
 //
